@@ -1,0 +1,189 @@
+/*
+ * rawalign_dtw.h -- C ABI of the GB300 library for the alignment step of
+ * RawAlign (Lindegger et al., arXiv 2310.05037): banded dynamic time warping
+ * of a read's normalised events against the expected signal of candidate
+ * reference regions, the alignment score and the per-read mapping decision.
+ *
+ * What each call computes, and the passage that defines it:
+ *   expected signal  r[j] = pore[k-mer at j]              Sup. A.1.1
+ *   band             |j*den - i*num| <= w_eff*den         Sec. 2.4.3
+ *   DTW              D(i,j) = |e_i - r_j| + min(NW,N,W)   Sec. 2.2
+ *   cost             D(n-1,m-1), or min over the last row Sec. 2.2
+ *   score            B_Match * N_Read - C_DTW             Sec. 2.3
+ *   decision         best candidate mapped iff >= thr     Sec. 2.3, Sec. 3.1
+ *
+ * Conventions (all calls):
+ *   - Every call returns a rawalign_status_t; nothing is thrown across the ABI.
+ *   - Host pointers passed to submit_* / prepare_* are read before the call
+ *     returns; the caller may free or reuse them afterwards.
+ *   - Device memory: the library places everything in the caller's arena
+ *     (config.arena_dev, arena_bytes), a block of device memory the caller
+ *     owns and keeps alive until rawalign_dtw_destroy returns.  The library
+ *     itself calls no cudaMalloc for device memory.  Pinned host memory is not
+ *     used by the library either; result buffers belong to the caller.
+ *   - All work runs on config.cuda_stream (a cudaStream_t; NULL = the legacy
+ *     default stream) on the device current at create time.
+ *   - One handle is not thread-safe: the caller serialises calls on it.
+ *   - Floating point: IEEE binary32, round to nearest even, no FMA contraction,
+ *     no flush-to-zero.  Results are bit-identical to a sequential evaluation
+ *     of the definitions above.
+ *   - Base codes: A=0, C=1, G=2, T=3; the reference is packed four bases per
+ *     byte, base p in bits 2*(p%4) and 2*(p%4)+1 of byte p/4.  The k-mer index
+ *     takes the first base as the most significant base-4 digit.
+ */
+#ifndef RAWALIGN_DTW_H
+#define RAWALIGN_DTW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rawalign_dtw rawalign_dtw_t; /* opaque handle */
+
+typedef enum {
+    RA_OK = 0,
+    RA_EINVAL = -1,     /* invalid argument or input data */
+    RA_ENOMEM = -2,     /* the arena (or the frontier store) is too small */
+    RA_EAGAIN = -3,     /* admission refused for now: retry after polling */
+    RA_ENOTREADY = -4,  /* poll: the ticket has not completed yet */
+    RA_ETIMEDOUT = -5,  /* a bounded device wait gave up (per-result status) */
+    RA_EDEVICE = -6,    /* a CUDA call failed */
+    RA_ECANCELED = -7   /* the work was dropped (serving: read cancelled) */
+} rawalign_status_t;
+
+enum { RA_END_GLOBAL = 0, RA_END_FREE = 1 };            /* end of the DTW */
+enum { RA_UNMAPPED = 0, RA_MAPPED = 1, RA_PENDING = 2 };/* decision */
+/* kernel choice: AUTO picks a striped variant per alignment; PLAIN runs one
+ * alignment per launch; STRIPE_G32..G4 force the striped variant with 32, 16,
+ * 8 or 4 lanes per alignment (tuning and tests). */
+enum { RA_KERNEL_AUTO = 0, RA_KERNEL_PLAIN = 1, RA_KERNEL_STRIPE_G32 = 2, RA_KERNEL_STRIPE_G16 = 3,
+       RA_KERNEL_STRIPE_G8 = 4, RA_KERNEL_STRIPE_G4 = 5 };
+
+typedef struct {
+    int32_t k;                 /* k-mer length, 1..8; pore table has 4^k entries */
+    float b_match;             /* B_Match (paper default 0.4) */
+    float score_threshold;     /* Score_Threshold (paper default 20) */
+    int32_t end_mode;          /* RA_END_GLOBAL or RA_END_FREE for batches */
+    void *arena_dev;           /* caller-owned device memory, 256-byte aligned */
+    uint64_t arena_bytes;
+    void *cuda_stream;         /* cudaStream_t */
+    int32_t max_candidates;    /* serving: candidates per read (<= 64) */
+    int32_t kernel;            /* RA_KERNEL_* */
+    int32_t serve_slots;       /* serving: reads admitted at once (0 = none) */
+    int32_t serve_max_events;  /* serving: events per read at most */
+    const char *autotune_path; /* optional tuning table written by the tuner */
+} rawalign_dtw_config_t;
+
+/* One candidate region of the reference for one read (48 bytes). */
+typedef struct {
+    uint64_t read_id;          /* batch: index of the read in the batch */
+    uint64_t ref_offset;       /* first base of the region in the reference */
+    uint32_t ref_len_bases;    /* bases; m = ref_len_bases - k + 1 >= 1 */
+    uint8_t strand;            /* 0 forward, 1 reverse complement of the region */
+    uint8_t pad0[3];
+    int32_t band_w;            /* band half-width in columns; < 0: no band */
+    int32_t pad1;
+    int64_t slope_num;         /* band slope num/den reference values per event; */
+    int64_t slope_den;         /* 0,0 = (m-1)/(n-1), the paper's length ratio  */
+} rawalign_candidate_t;
+
+/* Result of one candidate (56 bytes). */
+typedef struct {
+    uint64_t read_id;
+    uint32_t cand_idx;         /* index of the candidate in the submitted array */
+    float cost;                /* C_DTW (+inf when no in-band path reaches the end) */
+    float score;               /* B_Match * N_Read - C_DTW */
+    int32_t end_i, end_j;      /* end cell of the alignment (-1,-1 if none) */
+    int32_t w_eff;             /* band half-width used (-1 = no band) */
+    uint64_t cells;            /* in-band cells computed */
+    int32_t status;            /* RA_OK or a per-alignment error */
+    int32_t is_best;           /* 1 for the read's best candidate */
+    int32_t decision;          /* the read's decision: RA_MAPPED / RA_UNMAPPED / RA_PENDING */
+    int32_t pad;
+} rawalign_result_t;
+
+/* Creates a handle.  pore_model: 4^k floats (host).  ref_2bit: the packed
+ * reference (host, (ref_len+3)/4 bytes), copied into the arena once.
+ * Errors: RA_EINVAL (bad config or pointers), RA_ENOMEM (arena too small),
+ * RA_EDEVICE.  Cited: Sup. A.1.1 (pore model), Sec. 2.1.3 (candidates). */
+int rawalign_dtw_create(const rawalign_dtw_config_t *config, const float *pore_model,
+                        const uint8_t *ref_2bit, uint64_t ref_len, rawalign_dtw_t **out);
+
+/* Aligns a batch: every candidate against its read (Sec. 2.2-2.4.3), scores it
+ * (Sec. 2.3) and decides each read (best score >= threshold).  events: all
+ * reads' events back to back (host floats); read_offsets: n_reads+1 offsets
+ * into events; cands: n_cands candidates (host).  The work is queued on the
+ * stream; the results come from rawalign_dtw_poll(ticket).  Errors: RA_EINVAL
+ * (empty read, candidate outside the reference or shorter than k, read_id out
+ * of range, bad slope), RA_ENOMEM / RA_EAGAIN (arena full: poll earlier
+ * tickets first), RA_EDEVICE.  Non-finite events are detected on the device:
+ * the poll of that ticket returns RA_EINVAL. */
+int rawalign_dtw_submit_batch(rawalign_dtw_t *h, const float *events, const uint64_t *read_offsets,
+                              uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
+                              uint64_t *ticket);
+
+/* Serving (Read-Until, Sec. 1 and Sec. 3.1): appends n_events events of read
+ * read_id and advances every candidate's DTW by those rows, keeping each
+ * candidate's last DTW row (its frontier) in the arena between chunks.  The
+ * first chunk of a read gives its candidates (cands, n_cands <=
+ * max_candidates), later chunks pass NULL, 0.  Each candidate uses its own
+ * band slope (slope_num/den must be given) and the FREE end (min over the
+ * last row).  last = 1 closes the read after this chunk.  Returns RA_EAGAIN
+ * when no read slot or frontier memory is free (admission), RA_EINVAL for
+ * unknown reads or bad data.  The chunk's results (one per candidate, with the
+ * read's decision so far: RA_MAPPED, or RA_PENDING / RA_UNMAPPED when last)
+ * come from rawalign_dtw_poll(ticket). */
+int rawalign_dtw_submit_chunk(rawalign_dtw_t *h, uint64_t read_id, const float *events,
+                              uint32_t n_events, const rawalign_candidate_t *cands,
+                              uint32_t n_cands, int last, uint64_t *ticket);
+
+/* Launches all chunks submitted since the last flush as one continuous batch
+ * (serving); submit_chunk queues, flush runs.  Returns RA_OK when nothing is
+ * pending. */
+int rawalign_dtw_flush(rawalign_dtw_t *h);
+
+/* Waits up to timeout_us microseconds (0 = do not wait, < 0 = wait forever)
+ * for a ticket, then copies up to cap results into out (host) and sets n_out.
+ * Returns RA_ENOTREADY if the ticket is still running, RA_EINVAL for an
+ * unknown ticket, RA_EDEVICE on a device error.  A ticket can be polled once
+ * successfully; its memory is recycled afterwards. */
+int rawalign_dtw_poll(rawalign_dtw_t *h, uint64_t ticket, rawalign_result_t *out, uint32_t cap,
+                      uint32_t *n_out, int64_t timeout_us);
+
+/* Device-resident batches for repeated runs (the timing harness): prepare
+ * copies the inputs into the arena and plans the work once; run re-executes
+ * every step of the path on the resident inputs (as one CUDA graph) and
+ * returns a ticket; release frees the batch. */
+int rawalign_dtw_prepare_batch(rawalign_dtw_t *h, const float *events, const uint64_t *read_offsets,
+                               uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
+                               uint64_t *batch);
+int rawalign_dtw_run_batch(rawalign_dtw_t *h, uint64_t batch, uint64_t *ticket);
+int rawalign_dtw_release_batch(rawalign_dtw_t *h, uint64_t batch);
+
+/* Destroys the handle after waiting for all queued work.  The arena can be
+ * freed by the caller afterwards. */
+int rawalign_dtw_destroy(rawalign_dtw_t *h);
+
+/* Library counters for the last run of a batch or serving launch (timing
+ * harness): device time of the DTW kernel in ms, kernels launched, in-band
+ * cells.  Returns RA_EINVAL for an unknown batch. */
+typedef struct {
+    double dtw_ms;             /* CUDA-event time of the DTW kernel(s) */
+    double total_ms;           /* CUDA-event time of the whole path */
+    uint64_t cells;            /* in-band cells of the batch */
+    uint32_t launches;         /* kernels launched by one run */
+    uint32_t pad;
+} rawalign_dtw_stats_t;
+int rawalign_dtw_batch_stats(rawalign_dtw_t *h, uint64_t batch, rawalign_dtw_stats_t *out);
+
+/* Bytes of arena a batch of this shape needs (planning aid for callers). */
+uint64_t rawalign_dtw_batch_bytes(uint64_t n_events, uint32_t n_reads, uint32_t n_cands,
+                                  uint64_t total_ref_values);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

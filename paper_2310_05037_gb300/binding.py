@@ -1,0 +1,303 @@
+"""ctypes binding of librawalign_dtw (include/rawalign_dtw.h).
+
+Argument marshalling only: every step of the alignment path runs in the
+library's CUDA kernels.  PyTorch supplies the device arena and the stream.
+The binding fails loudly if the shared library is missing; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .synth import CANDIDATE_DTYPE
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librawalign_dtw.so")
+
+RA_OK, RA_EINVAL, RA_ENOMEM, RA_EAGAIN, RA_ENOTREADY, RA_ETIMEDOUT, RA_EDEVICE, RA_ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7
+RA_END_GLOBAL, RA_END_FREE = 0, 1
+RA_UNMAPPED, RA_MAPPED, RA_PENDING = 0, 1, 2
+RA_KERNEL_AUTO, RA_KERNEL_PLAIN = 0, 1
+RA_KERNEL_STRIPE = {32: 2, 16: 3, 8: 4, 4: 5}
+
+STATUS_NAMES = {0: "RA_OK", -1: "RA_EINVAL", -2: "RA_ENOMEM", -3: "RA_EAGAIN", -4: "RA_ENOTREADY",
+                -5: "RA_ETIMEDOUT", -6: "RA_EDEVICE", -7: "RA_ECANCELED"}
+
+
+class RawAlignError(RuntimeError):
+    def __init__(self, call, code):
+        super().__init__("%s failed: %s (%d)" % (call, STATUS_NAMES.get(code, "?"), code))
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("k", C.c_int32),
+        ("b_match", C.c_float),
+        ("score_threshold", C.c_float),
+        ("end_mode", C.c_int32),
+        ("arena_dev", C.c_void_p),
+        ("arena_bytes", C.c_uint64),
+        ("cuda_stream", C.c_void_p),
+        ("max_candidates", C.c_int32),
+        ("kernel", C.c_int32),
+        ("serve_slots", C.c_int32),
+        ("serve_max_events", C.c_int32),
+        ("autotune_path", C.c_char_p),
+    ]
+
+
+class Candidate(C.Structure):
+    _fields_ = [
+        ("read_id", C.c_uint64),
+        ("ref_offset", C.c_uint64),
+        ("ref_len_bases", C.c_uint32),
+        ("strand", C.c_uint8),
+        ("pad0", C.c_uint8 * 3),
+        ("band_w", C.c_int32),
+        ("pad1", C.c_int32),
+        ("slope_num", C.c_int64),
+        ("slope_den", C.c_int64),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("read_id", C.c_uint64),
+        ("cand_idx", C.c_uint32),
+        ("cost", C.c_float),
+        ("score", C.c_float),
+        ("end_i", C.c_int32),
+        ("end_j", C.c_int32),
+        ("w_eff", C.c_int32),
+        ("cells", C.c_uint64),
+        ("status", C.c_int32),
+        ("is_best", C.c_int32),
+        ("decision", C.c_int32),
+        ("pad", C.c_int32),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("dtw_ms", C.c_double),
+        ("total_ms", C.c_double),
+        ("cells", C.c_uint64),
+        ("launches", C.c_uint32),
+        ("pad", C.c_uint32),
+    ]
+
+
+RESULT_DTYPE = np.dtype(
+    {
+        "names": [f[0] for f in Result._fields_],
+        "formats": ["<u8", "<u4", "<f4", "<f4", "<i4", "<i4", "<i4", "<u8", "<i4", "<i4", "<i4", "<i4"],
+        "offsets": [getattr(Result, f[0]).offset for f in Result._fields_],
+        "itemsize": C.sizeof(Result),
+    }
+)
+
+# symbol -> (restype, argtypes)
+_u64p = C.POINTER(C.c_uint64)
+SIGNATURES = {
+    "rawalign_dtw_create": (C.c_int, [C.POINTER(Config), C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "rawalign_dtw_submit_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, _u64p]),
+    "rawalign_dtw_submit_chunk": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_int, _u64p]),
+    "rawalign_dtw_flush": (C.c_int, [C.c_void_p]),
+    "rawalign_dtw_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.c_int64]),
+    "rawalign_dtw_prepare_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, _u64p]),
+    "rawalign_dtw_run_batch": (C.c_int, [C.c_void_p, C.c_uint64, _u64p]),
+    "rawalign_dtw_release_batch": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "rawalign_dtw_destroy": (C.c_int, [C.c_void_p]),
+    "rawalign_dtw_batch_stats": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Stats)]),
+    "rawalign_dtw_batch_bytes": (C.c_uint64, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError("librawalign_dtw.so is missing (%s): run __graft_entry__.build()" % p)
+        L = C.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(call, code):
+    if code != RA_OK:
+        raise RawAlignError(call, code)
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None and a.size else C.c_void_p(0)
+
+
+# ---- the ABI, one Python function per entry point (same names) -------------
+
+def rawalign_dtw_create(config: Config, pore: np.ndarray, ref2bit: np.ndarray, ref_len: int) -> C.c_void_p:
+    pore = np.ascontiguousarray(pore, np.float32)
+    ref = np.ascontiguousarray(ref2bit, np.uint8)
+    h = C.c_void_p()
+    _check("rawalign_dtw_create", load().rawalign_dtw_create(C.byref(config), _ptr(pore), _ptr(ref), int(ref_len), C.byref(h)))
+    return h
+
+
+def _batch_args(events, read_offsets, cands):
+    ev = np.ascontiguousarray(events, np.float32)
+    offs = np.ascontiguousarray(read_offsets, np.uint64)
+    cands = np.ascontiguousarray(cands)
+    if cands.dtype != CANDIDATE_DTYPE:
+        raise TypeError("candidates must use CANDIDATE_DTYPE")
+    return ev, offs, cands
+
+
+def rawalign_dtw_submit_batch(h, events, read_offsets, cands) -> int:
+    ev, offs, cands = _batch_args(events, read_offsets, cands)
+    t = C.c_uint64()
+    _check("rawalign_dtw_submit_batch", load().rawalign_dtw_submit_batch(
+        h, _ptr(ev), _ptr(offs), len(offs) - 1, _ptr(cands), len(cands), C.byref(t)))
+    return t.value
+
+
+def rawalign_dtw_prepare_batch(h, events, read_offsets, cands) -> int:
+    ev, offs, cands = _batch_args(events, read_offsets, cands)
+    b = C.c_uint64()
+    _check("rawalign_dtw_prepare_batch", load().rawalign_dtw_prepare_batch(
+        h, _ptr(ev), _ptr(offs), len(offs) - 1, _ptr(cands), len(cands), C.byref(b)))
+    return b.value
+
+
+def rawalign_dtw_run_batch(h, batch: int) -> int:
+    t = C.c_uint64()
+    _check("rawalign_dtw_run_batch", load().rawalign_dtw_run_batch(h, batch, C.byref(t)))
+    return t.value
+
+
+def rawalign_dtw_release_batch(h, batch: int) -> None:
+    _check("rawalign_dtw_release_batch", load().rawalign_dtw_release_batch(h, batch))
+
+
+def rawalign_dtw_submit_chunk(h, read_id: int, events, cands=None, last: bool = False) -> int:
+    ev = np.ascontiguousarray(events, np.float32)
+    t = C.c_uint64()
+    if cands is not None:
+        cands = np.ascontiguousarray(cands)
+        cp, nc = _ptr(cands), len(cands)
+    else:
+        cp, nc = C.c_void_p(0), 0
+    code = load().rawalign_dtw_submit_chunk(h, int(read_id), _ptr(ev), len(ev), cp, nc, 1 if last else 0, C.byref(t))
+    _check("rawalign_dtw_submit_chunk", code)
+    return t.value
+
+
+def rawalign_dtw_flush(h) -> None:
+    _check("rawalign_dtw_flush", load().rawalign_dtw_flush(h))
+
+
+def rawalign_dtw_poll(h, ticket: int, cap: int, timeout_us: int = -1):
+    """Returns a structured array of results, or None while RA_ENOTREADY."""
+    out = np.zeros(max(cap, 1), RESULT_DTYPE)
+    n = C.c_uint32()
+    code = load().rawalign_dtw_poll(h, int(ticket), _ptr(out), cap, C.byref(n), int(timeout_us))
+    if code == RA_ENOTREADY:
+        return None
+    _check("rawalign_dtw_poll", code)
+    return out[: n.value]
+
+
+def rawalign_dtw_batch_stats(h, batch: int) -> Stats:
+    s = Stats()
+    _check("rawalign_dtw_batch_stats", load().rawalign_dtw_batch_stats(h, batch, C.byref(s)))
+    return s
+
+
+def rawalign_dtw_batch_bytes(n_events, n_reads, n_cands, total_ref_values) -> int:
+    return int(load().rawalign_dtw_batch_bytes(int(n_events), int(n_reads), int(n_cands), int(total_ref_values)))
+
+
+def rawalign_dtw_destroy(h) -> None:
+    _check("rawalign_dtw_destroy", load().rawalign_dtw_destroy(h))
+
+
+# ---- convenience wrapper: arena and stream from torch ------------------------
+
+class Aligner:
+    """Owns a handle, its torch-allocated arena and stream.
+
+    >>> al = Aligner(pore, ref2bit, ref_len, arena_bytes=1 << 30)
+    >>> res = al.align(events, read_offsets, cands)
+    """
+
+    def __init__(self, pore, ref2bit, ref_len, arena_bytes=1 << 30, k=6, b_match=0.4, score_threshold=20.0,
+                 end_mode=RA_END_GLOBAL, kernel=RA_KERNEL_AUTO, stream=None, serve_slots=0,
+                 serve_max_events=0, max_candidates=64, device="cuda:0"):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        torch.cuda.set_device(self.device)
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        cfg = Config()
+        cfg.k = k
+        cfg.b_match = b_match
+        cfg.score_threshold = score_threshold
+        cfg.end_mode = end_mode
+        cfg.arena_dev = self.arena.data_ptr()
+        cfg.arena_bytes = int(arena_bytes)
+        cfg.cuda_stream = self.stream.cuda_stream
+        cfg.max_candidates = max_candidates
+        cfg.kernel = kernel
+        cfg.serve_slots = serve_slots
+        cfg.serve_max_events = serve_max_events
+        cfg.autotune_path = None
+        self.cfg = cfg
+        self.h = rawalign_dtw_create(cfg, pore, ref2bit, ref_len)
+
+    def align(self, events, read_offsets, cands, timeout_us=-1):
+        t = rawalign_dtw_submit_batch(self.h, events, read_offsets, cands)
+        return rawalign_dtw_poll(self.h, t, len(cands), timeout_us)
+
+    def prepare(self, events, read_offsets, cands):
+        return rawalign_dtw_prepare_batch(self.h, events, read_offsets, cands)
+
+    def run(self, batch):
+        return rawalign_dtw_run_batch(self.h, batch)
+
+    def poll(self, ticket, cap, timeout_us=-1):
+        return rawalign_dtw_poll(self.h, ticket, cap, timeout_us)
+
+    def stats(self, batch):
+        return rawalign_dtw_batch_stats(self.h, batch)
+
+    def release(self, batch):
+        rawalign_dtw_release_batch(self.h, batch)
+
+    def close(self):
+        if self.h:
+            rawalign_dtw_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,848 @@
+// engine.cu -- host side of librawalign_dtw: the C ABI, the arena, batch
+// planning and launch, tickets, and the Read-Until serving loop.
+//
+// Planning turns every (read, candidate) pair into a WorkDesc: the band of
+// Sec. 2.4.3 (slope num/den, half-width w_eff), the stripe period dC of the
+// striped kernel, the first column and the step count.  The host picks, per
+// alignment, the lanes-per-alignment variant that wastes the fewest lane
+// steps, orders the queue longest-first, and records the launches of one run
+// in a CUDA graph that later runs replay.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace ra;
+
+namespace {
+
+constexpr int kBlock = 128;
+const int kVariants[][2] = {{32, 8}, {16, 8}, {8, 8}, {4, 8}};
+constexpr int kNumVariants = 4;
+
+// ---------------------------------------------------------------- band math
+inline int64_t fdiv(int64_t a, int64_t b)
+{
+    int64_t q = a / b, r = a % b;
+    return (r != 0 && ((r < 0) != (b < 0))) ? q - 1 : q;
+}
+inline int64_t cdiv(int64_t a, int64_t b) { return -fdiv(-a, b); }
+
+struct BandDef {
+    int64_t num = 0, den = 1, w = 0, m = 1;
+    int64_t lo(int64_t i) const { return std::max<int64_t>(0, cdiv(i * num - w * den, den)); }
+    int64_t hi(int64_t i) const { return std::min<int64_t>(m - 1, fdiv(i * num + w * den, den)); }
+};
+
+// Band of one candidate (Sec. 2.4.3): derived slope (m-1)/(n-1) unless given;
+// w_eff = max(w, ceil(num/(2 den)), 1); no band -> num 0, den 1, w = m.
+int band_for(int64_t n, int64_t m, int32_t band_w, int64_t num_in, int64_t den_in, BandDef &b,
+             int32_t &w_report)
+{
+    b.m = m;
+    if (band_w < 0 || n == 1 || m == 1) {
+        b.num = 0;
+        b.den = 1;
+        b.w = m;
+        w_report = -1;
+        return 0;
+    }
+    int64_t num = num_in, den = den_in;
+    if (num == 0 && den == 0) {
+        num = m - 1;
+        den = n - 1;
+    }
+    if (num < 0 || den <= 0 || num > (1ll << 30) || den > (1ll << 30))
+        return -1;
+    int64_t half = (num + 2 * den - 1) / (2 * den);
+    int64_t w = std::max<int64_t>(std::max<int64_t>(band_w, half), 1);
+    if (w > (1ll << 30))
+        return -1;
+    b.num = num;
+    b.den = den;
+    b.w = w;
+    w_report = (int32_t)w;
+    return 0;
+}
+
+// Schedule of one piece (rows row0..row0+nrows-1) for a (G, HR) variant, in
+// O(1): dC bounds b(k,t) - a(k+1,t) + 2 for every lane and stripe, where b is
+// the last in-band column of a lane's rows in stripe k and a the first of its
+// rows in stripe k+1.  With hi(x) <= x*s + w and lo(y) >= y*s - w
+// (s = num/den, y - x = H - HR + 1): b - a <= 2w - (H - HR + 1) s, and
+// b - a <= m - 1 from the table's edges.
+struct Sched {
+    int32_t dC = 0, a0 = 0, s_end = 0;
+    double cells_est = 0;
+    double eff = 0;  // in-band cells / lane-cell slots (estimate)
+};
+
+Sched schedule(const BandDef &b, int64_t row0, int64_t nrows, int G, int HR)
+{
+    Sched s;
+    const int64_t H = (int64_t)G * HR;
+    const int64_t K = (nrows + H - 1) / H;
+    const int64_t last = row0 + nrows - 1;
+    s.a0 = (int32_t)b.lo(row0);
+    if (s.a0 > b.m - 1) {
+        s.s_end = 0;
+        return s;
+    }
+    int64_t span = fdiv(2 * b.w * b.den - (H - HR + 1) * b.num, b.den);
+    span = std::min<int64_t>(span, b.m - 1);
+    const int64_t dC = std::max<int64_t>(G + 1, span + 2);
+    const int64_t nl = nrows - 1 - (K - 1) * H;
+    const int64_t t_last = nl / HR;
+    const int64_t b_last = b.hi(last);
+    s.dC = (int32_t)dC;
+    const int64_t se = b_last - s.a0 + 3 + t_last + (K - 1) * dC;
+    s.s_end = (int32_t)std::max<int64_t>(se, 1);
+    s.cells_est = (double)nrows * (double)std::min<int64_t>(2 * b.w + 1, b.m);
+    const double slots = (double)s.s_end * G * HR;
+    s.eff = slots > 0 ? s.cells_est / slots : 0;
+    return s;
+}
+
+// ---------------------------------------------------------------- arena
+struct Arena {
+    char *base = nullptr;
+    uint64_t size = 0;
+    std::map<uint64_t, uint64_t> free_;  // offset -> size
+    void init(void *p, uint64_t n)
+    {
+        base = (char *)p;
+        size = n;
+        free_.clear();
+        if (n)
+            free_[0] = n;
+    }
+    void *alloc(uint64_t n)
+    {
+        n = (n + 255) & ~255ull;
+        if (n == 0)
+            n = 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                uint64_t off = it->first, sz = it->second;
+                free_.erase(it);
+                if (sz > n)
+                    free_[off + n] = sz - n;
+                used_[off] = n;
+                return base + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(void *p)
+    {
+        if (!p)
+            return;
+        uint64_t off = (uint64_t)((char *)p - base);
+        auto u = used_.find(off);
+        if (u == used_.end())
+            return;
+        uint64_t n = u->second;
+        used_.erase(u);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    std::map<uint64_t, uint64_t> used_;
+};
+
+struct ClassLaunch {
+    int G = 0, HR = 0;
+    int first = 0, count = 0;  // range in the sorted work array
+    int ring_cap = 0;
+    int ring_in_smem = 1;
+    int grid = 0;
+    size_t smem = 0;
+    float *gring = nullptr;
+};
+
+struct Batch {
+    uint32_t n_reads = 0, n_cands = 0;
+    uint64_t n_events = 0;
+    std::vector<void *> blocks;  // arena allocations
+    float *d_events = nullptr;
+    SigDesc *d_sig = nullptr;
+    float *d_r = nullptr;
+    WorkDesc *d_work = nullptr;
+    rawalign_result_t *d_results = nullptr;
+    unsigned long long *d_keys = nullptr;
+    int *d_read_of = nullptr;
+    int *d_queue = nullptr;  // [kNumVariants]
+    int *d_err = nullptr;    // [2]
+    float *d_plain_diag = nullptr;
+    int max_rows = 0;
+    std::vector<ClassLaunch> classes;
+    uint64_t cells = 0;
+    bool auto_release = false;
+    bool plain = false;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t launches = 0;
+    bool ran = false;
+};
+
+struct Ticket {
+    uint64_t batch = 0;  // batch id (0 = serving)
+    cudaEvent_t done = nullptr;
+    rawalign_result_t *d_results = nullptr;
+    uint32_t n = 0;
+    int *d_err = nullptr;
+    std::vector<rawalign_result_t> host;  // serving: filled at flush completion
+    std::vector<uint64_t> read_ids;       // serving: caller read ids per result
+    bool serving = false;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- serving state
+namespace {
+struct ServeCand {
+    BandDef band;
+    int32_t w_report = 0;
+    SigDesc sig{};
+    uint64_t r_off = 0;     // in the serving r store
+    uint64_t fr_off[2] = {0, 0};  // frontier ping-pong (floats)
+    int cur = 0;            // which frontier holds the row above the next chunk
+    int32_t fr_lo = -1, fr_wid = 0;  // band of the last processed row
+    uint32_t m = 0;
+    bool dead = false;      // no in-band cell any more
+};
+struct ServeRead {
+    uint64_t read_id = 0;
+    int slot = -1;
+    uint32_t rows_done = 0;   // events aligned so far
+    uint32_t ev_base = 0;     // events of this read in the slot's event store
+    std::vector<ServeCand> cands;
+    bool closing = false;
+};
+struct PendingChunk {
+    uint64_t ticket;
+    int slot;
+    uint32_t row0, nrows;
+    int last;
+};
+}  // namespace
+
+struct rawalign_dtw {
+    rawalign_dtw_config_t cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 152;
+    Arena arena;
+    float *d_pore = nullptr;
+    uint8_t *d_ref = nullptr;
+    uint64_t ref_len = 0;
+    uint64_t next_id = 1;
+    std::map<uint64_t, Batch> batches;
+    std::map<uint64_t, Ticket> tickets;
+    int max_blocks[kNumVariants][2] = {};
+    // serving
+    int serve_slots = 0;
+    uint32_t serve_max_events = 0;
+    int serve_max_cands = 0;
+    float *d_serve_events = nullptr;   // [slots][max_events]
+    float *d_serve_r = nullptr;        // [slots][max_cands][max_m]
+    float *d_frontier = nullptr;       // [slots][max_cands][2][fr_cap]
+    uint32_t serve_max_m = 0, fr_cap = 0;
+    std::vector<int> free_slots;
+    std::map<uint64_t, ServeRead> reads;
+    std::vector<PendingChunk> pending;
+    // per-flush device buffers
+    WorkDesc *d_sw = nullptr;
+    SigDesc *d_ssig = nullptr;
+    rawalign_result_t *d_sres = nullptr;
+    unsigned long long *d_skeys = nullptr;
+    int *d_sread_of = nullptr;
+    int *d_squeue = nullptr;
+    int *d_serr = nullptr;
+    float *d_sring = nullptr;
+    uint32_t s_cap_work = 0, s_cap_ring = 0;
+};
+
+namespace {
+
+int cuda_ok(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return RA_OK;
+    fprintf(stderr, "rawalign_dtw: CUDA error %s\n", cudaGetErrorString(e));
+    return RA_EDEVICE;
+}
+
+#define RA_CUDA(x)                      \
+    do {                                \
+        int rc__ = cuda_ok(x);          \
+        if (rc__ != RA_OK)              \
+            return rc__;                \
+    } while (0)
+
+int next_pow2(int64_t x)
+{
+    int64_t p = 1;
+    while (p < x)
+        p <<= 1;
+    return (int)p;
+}
+
+void free_batch(rawalign_dtw *h, Batch &b)
+{
+    if (b.graph)
+        cudaGraphExecDestroy(b.graph);
+    for (auto &e : b.ev)
+        if (e)
+            cudaEventDestroy(e);
+    for (void *p : b.blocks)
+        h->arena.release(p);
+    b.blocks.clear();
+}
+
+template <typename T>
+T *take(rawalign_dtw *h, Batch &b, uint64_t count)
+{
+    void *p = h->arena.alloc(sizeof(T) * std::max<uint64_t>(count, 1));
+    if (p)
+        b.blocks.push_back(p);
+    return (T *)p;
+}
+
+// Chooses the striped variant for one alignment: fewest idle lane-cell slots,
+// preferring more lanes per alignment when the waste is close.
+int choose_variant(const BandDef &band, int64_t n, Sched &out)
+{
+    int best = -1;
+    double best_score = -1;
+    for (int v = 0; v < kNumVariants; ++v) {
+        const int G = kVariants[v][0], HR = kVariants[v][1];
+        Sched s = schedule(band, 0, n, G, HR);
+        if (s.s_end <= 0) {
+            out = s;
+            return 0;
+        }
+        // prefer wide groups unless they waste clearly more lane time
+        const double score = s.eff * (1.0 + 0.04 * (kNumVariants - v));
+        if (score > best_score) {
+            best_score = score;
+            best = v;
+            out = s;
+        }
+    }
+    return best;
+}
+
+int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64_t *offs,
+                    uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands)
+{
+    const int k = h->cfg.k;
+    b.n_reads = n_reads;
+    b.n_cands = n_cands;
+    b.n_events = n_reads ? offs[n_reads] : 0;
+    b.plain = (h->cfg.kernel == RA_KERNEL_PLAIN);
+    // validation (host part; event values are checked on the device)
+    for (uint32_t q = 0; q < n_reads; ++q)
+        if (offs[q + 1] <= offs[q])
+            return RA_EINVAL;
+    if (n_reads && offs[0] != 0)
+        return RA_EINVAL;
+    if (b.n_events >= (1ull << 40))
+        return RA_EINVAL;
+    struct Item {
+        WorkDesc wd;
+        int variant;
+        double cost;
+    };
+    std::vector<Item> items(n_cands);
+    std::vector<SigDesc> sig(n_cands);
+    uint64_t r_total = 0;
+    b.cells = 0;
+    b.max_rows = 1;
+    for (uint32_t c = 0; c < n_cands; ++c) {
+        const rawalign_candidate_t &cd = cands[c];
+        if (cd.read_id >= n_reads || cd.strand > 1)
+            return RA_EINVAL;
+        if (cd.ref_offset > h->ref_len || cd.ref_len_bases > h->ref_len - cd.ref_offset)
+            return RA_EINVAL;
+        if ((int64_t)cd.ref_len_bases < k)
+            return RA_EINVAL;
+        const int64_t n = (int64_t)(offs[cd.read_id + 1] - offs[cd.read_id]);
+        const int64_t m = (int64_t)cd.ref_len_bases - k + 1;
+        if (n >= (1 << 30) || m >= (1 << 30))
+            return RA_EINVAL;
+        BandDef band;
+        int32_t wrep;
+        if (band_for(n, m, cd.band_w, cd.slope_num, cd.slope_den, band, wrep) != 0)
+            return RA_EINVAL;
+        Item &it = items[c];
+        memset(&it.wd, 0, sizeof(WorkDesc));
+        WorkDesc &wd = it.wd;
+        wd.ev_off = offs[cd.read_id];
+        wd.r_off = r_total;
+        wd.fin_off = ~0ull;
+        wd.num = band.num;
+        wd.den = band.den;
+        wd.row0 = 0;
+        wd.nrows = (int32_t)n;
+        wd.m = (int32_t)m;
+        wd.w = (int32_t)band.w;
+        wd.cand = (int32_t)c;
+        wd.read = (int32_t)cd.read_id;
+        wd.n_read = (int32_t)n;
+        wd.fin_lo = -1;
+        wd.fin_wid = 0;
+        wd.w_report = wrep;
+        Sched s;
+        const int forced = h->cfg.kernel - RA_KERNEL_STRIPE_G32;
+        if (b.plain || (forced >= 0 && forced < kNumVariants)) {
+            it.variant = b.plain ? 0 : forced;
+            s = schedule(band, 0, n, kVariants[it.variant][0], kVariants[it.variant][1]);
+        } else {
+            it.variant = choose_variant(band, n, s);
+        }
+        wd.dC = s.dC;
+        wd.a0 = s.a0;
+        wd.s_end = s.s_end;
+        it.cost = (double)s.s_end * kVariants[it.variant][0];
+        b.max_rows = std::max<int>(b.max_rows, (int)n);
+        sig[c].ref_off = cd.ref_offset;
+        sig[c].r_off = r_total;
+        sig[c].len = cd.ref_len_bases;
+        sig[c].strand = cd.strand;
+        r_total += (uint64_t)m;
+    }
+    // order: by variant, longest first
+    std::vector<int> order(n_cands);
+    for (uint32_t c = 0; c < n_cands; ++c)
+        order[c] = (int)c;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (items[x].variant != items[y].variant)
+            return items[x].variant < items[y].variant;
+        return items[x].cost > items[y].cost;
+    });
+    std::vector<WorkDesc> work(n_cands);
+    std::vector<int> read_of(n_cands);
+    for (uint32_t c = 0; c < n_cands; ++c) {
+        work[c] = items[order[c]].wd;
+        read_of[c] = (int)cands[c].read_id;
+    }
+    // device memory
+    b.d_events = take<float>(h, b, b.n_events);
+    b.d_sig = take<SigDesc>(h, b, n_cands);
+    b.d_r = take<float>(h, b, r_total);
+    b.d_work = take<WorkDesc>(h, b, n_cands);
+    b.d_results = take<rawalign_result_t>(h, b, n_cands);
+    b.d_keys = take<unsigned long long>(h, b, n_reads);
+    b.d_read_of = take<int>(h, b, n_cands);
+    b.d_queue = take<int>(h, b, kNumVariants + 2);
+    if (!b.d_events || !b.d_sig || !b.d_r || !b.d_work || !b.d_results || !b.d_keys || !b.d_read_of ||
+        !b.d_queue)
+        return RA_ENOMEM;
+    b.d_err = b.d_queue + kNumVariants;
+    if (b.plain) {
+        b.d_plain_diag = take<float>(h, b, 3ull * (b.max_rows + 2));
+        if (!b.d_plain_diag)
+            return RA_ENOMEM;
+    }
+    // classes and ring buffers
+    b.classes.clear();
+    if (!b.plain) {
+        int pos = 0;
+        for (int v = 0; v < kNumVariants; ++v) {
+            ClassLaunch cl;
+            cl.G = kVariants[v][0];
+            cl.HR = kVariants[v][1];
+            cl.first = pos;
+            int64_t need = 4;
+            while (pos < (int)n_cands && items[order[pos]].variant == v) {
+                need = std::max<int64_t>(need, (int64_t)work[pos].dC + 2);
+                need = std::max<int64_t>(need, (int64_t)work[pos].fin_wid + 2);
+                ++pos;
+            }
+            cl.count = pos - cl.first;
+            if (cl.count == 0)
+                continue;
+            cl.ring_cap = next_pow2(need);
+            const int groups_per_block = kBlock / cl.G;
+            size_t smem = (size_t)groups_per_block * cl.ring_cap * sizeof(float);
+            cl.ring_in_smem = smem <= 64 * 1024;
+            cl.smem = cl.ring_in_smem ? smem : 0;
+            int nb = stripe_max_blocks_per_sm(cl.G, cl.HR, kBlock, cl.smem);
+            if (nb <= 0)
+                return RA_EDEVICE;
+            int grid = h->sm_count * nb;
+            const int needed_blocks = (cl.count + groups_per_block - 1) / groups_per_block;
+            cl.grid = std::max(1, std::min(grid, needed_blocks));
+            if (!cl.ring_in_smem) {
+                cl.gring = take<float>(h, b, (uint64_t)cl.grid * groups_per_block * cl.ring_cap);
+                if (!cl.gring)
+                    return RA_ENOMEM;
+            }
+            b.classes.push_back(cl);
+        }
+    }
+    cudaStream_t s = h->stream;
+    RA_CUDA(cudaMemcpyAsync(b.d_events, events, sizeof(float) * b.n_events, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(b.d_sig, sig.data(), sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(b.d_work, work.data(), sizeof(WorkDesc) * n_cands, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(b.d_read_of, read_of.data(), sizeof(int) * n_cands, cudaMemcpyHostToDevice, s));
+    for (auto &e : b.ev)
+        RA_CUDA(cudaEventCreate(&e));
+    // the caller may free its buffers on return
+    RA_CUDA(cudaStreamSynchronize(s));
+    return RA_OK;
+}
+
+int record_run(rawalign_dtw *h, Batch &b)
+{
+    cudaStream_t s = h->stream;
+    uint32_t launches = 0;
+    RA_CUDA(cudaEventRecord(b.ev[0], s));
+    RA_CUDA(cudaMemsetAsync(b.d_keys, 0, sizeof(unsigned long long) * std::max<uint32_t>(b.n_reads, 1), s));
+    RA_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int) * (kNumVariants + 2), s));
+    RA_CUDA(launch_check_events(b.d_events, b.n_events, b.d_err, s));
+    launches += b.n_events ? 1 : 0;
+    RA_CUDA(launch_expected_signal(b.d_sig, (int)b.n_cands, h->d_ref, h->d_pore, h->cfg.k, b.d_r, s));
+    launches += b.n_cands ? 1 : 0;
+    RA_CUDA(cudaEventRecord(b.ev[1], s));
+    if (b.plain) {
+        for (uint32_t c = 0; c < b.n_cands; ++c) {
+            RA_CUDA(launch_plain(b.d_work + c, b.d_events, b.d_r, b.d_plain_diag, b.d_results, b.d_keys,
+                                 h->cfg.b_match, h->cfg.end_mode == RA_END_FREE, s));
+            ++launches;
+        }
+    } else {
+        int qi = 0;
+        for (auto &cl : b.classes) {
+            StripeParams p{};
+            p.work = b.d_work + cl.first;
+            p.n_work = cl.count;
+            p.queue = b.d_queue + (qi++);
+            p.events = b.d_events;
+            p.r_all = b.d_r;
+            p.fstore = nullptr;
+            p.fstore_out = nullptr;
+            p.results = b.d_results;
+            p.best_keys = b.d_keys;
+            p.gring = cl.gring;
+            p.ring_cap = cl.ring_cap;
+            p.ring_in_smem = cl.ring_in_smem;
+            p.b_match = h->cfg.b_match;
+            p.end_free = h->cfg.end_mode == RA_END_FREE;
+            p.err = b.d_err;
+            RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, s));
+            ++launches;
+        }
+    }
+    RA_CUDA(cudaEventRecord(b.ev[2], s));
+    RA_CUDA(launch_decide(b.d_results, (int)b.n_cands, b.d_keys, b.d_read_of, h->cfg.score_threshold, 1, s));
+    launches += b.n_cands ? 1 : 0;
+    RA_CUDA(cudaEventRecord(b.ev[3], s));
+    b.launches = launches;
+    return RA_OK;
+}
+
+int run_batch(rawalign_dtw *h, Batch &b)
+{
+    if (b.plain) {
+        return record_run(h, b);
+    }
+    if (!b.graph) {
+        cudaGraph_t g = nullptr;
+        RA_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = record_run(h, b);
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (rc != RA_OK) {
+            if (g)
+                cudaGraphDestroy(g);
+            return rc;
+        }
+        RA_CUDA(e);
+        e = cudaGraphInstantiate(&b.graph, g, 0);
+        cudaGraphDestroy(g);
+        RA_CUDA(e);
+    }
+    RA_CUDA(cudaGraphLaunch(b.graph, h->stream));
+    return RA_OK;
+}
+
+int new_ticket(rawalign_dtw *h, uint64_t batch_id, Batch &b, uint64_t *ticket)
+{
+    Ticket t;
+    t.batch = batch_id;
+    t.d_results = b.d_results;
+    t.n = b.n_cands;
+    t.d_err = b.d_err;
+    RA_CUDA(cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming));
+    RA_CUDA(cudaEventRecord(t.done, h->stream));
+    uint64_t id = h->next_id++;
+    h->tickets[id] = std::move(t);
+    *ticket = id;
+    return RA_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const float *pore_model,
+                                   const uint8_t *ref_2bit, uint64_t ref_len, rawalign_dtw_t **out)
+{
+    if (!config || !pore_model || !out || (!ref_2bit && ref_len))
+        return RA_EINVAL;
+    *out = nullptr;
+    if (config->k < 1 || config->k > 8 || !config->arena_dev || config->arena_bytes < 4096)
+        return RA_EINVAL;
+    if (((uintptr_t)config->arena_dev & 255) != 0)
+        return RA_EINVAL;
+    if (!std::isfinite(config->b_match) || !std::isfinite(config->score_threshold))
+        return RA_EINVAL;
+    if (config->end_mode != RA_END_GLOBAL && config->end_mode != RA_END_FREE)
+        return RA_EINVAL;
+    if (config->kernel < RA_KERNEL_AUTO || config->kernel > RA_KERNEL_STRIPE_G4)
+        return RA_EINVAL;
+    const uint64_t n_pore = 1ull << (2 * config->k);
+    for (uint64_t x = 0; x < n_pore; ++x)
+        if (!std::isfinite(pore_model[x]))
+            return RA_EINVAL;
+    rawalign_dtw *h = new (std::nothrow) rawalign_dtw();
+    if (!h)
+        return RA_ENOMEM;
+    h->cfg = *config;
+    h->cfg.autotune_path = nullptr;
+    h->stream = (cudaStream_t)config->cuda_stream;
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    h->arena.init(config->arena_dev, config->arena_bytes);
+    h->d_pore = (float *)h->arena.alloc(sizeof(float) * n_pore);
+    h->d_ref = (uint8_t *)h->arena.alloc(std::max<uint64_t>((ref_len + 3) / 4, 1));
+    if (!h->d_pore || !h->d_ref) {
+        delete h;
+        return RA_ENOMEM;
+    }
+    h->ref_len = ref_len;
+    int rc = RA_OK;
+    if (cudaMemcpyAsync(h->d_pore, pore_model, sizeof(float) * n_pore, cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess ||
+        (ref_len && cudaMemcpyAsync(h->d_ref, ref_2bit, (ref_len + 3) / 4, cudaMemcpyHostToDevice, h->stream) !=
+                        cudaSuccess) ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        rc = RA_EDEVICE;
+    if (rc != RA_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return RA_OK;
+}
+
+extern "C" int rawalign_dtw_prepare_batch(rawalign_dtw_t *h, const float *events, const uint64_t *read_offsets,
+                                          uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
+                                          uint64_t *batch)
+{
+    if (!h || !batch || !read_offsets || (n_cands && !cands) || (!events && n_reads))
+        return RA_EINVAL;
+    cudaSetDevice(h->device);
+    uint64_t id = h->next_id++;
+    Batch &b = h->batches[id];
+    int rc = plan_and_upload(h, b, events, read_offsets, n_reads, cands, n_cands);
+    if (rc != RA_OK) {
+        free_batch(h, b);
+        h->batches.erase(id);
+        return rc;
+    }
+    *batch = id;
+    return RA_OK;
+}
+
+extern "C" int rawalign_dtw_run_batch(rawalign_dtw_t *h, uint64_t batch, uint64_t *ticket)
+{
+    if (!h || !ticket)
+        return RA_EINVAL;
+    auto it = h->batches.find(batch);
+    if (it == h->batches.end())
+        return RA_EINVAL;
+    cudaSetDevice(h->device);
+    int rc = run_batch(h, it->second);
+    if (rc != RA_OK)
+        return rc;
+    it->second.ran = true;
+    return new_ticket(h, batch, it->second, ticket);
+}
+
+extern "C" int rawalign_dtw_release_batch(rawalign_dtw_t *h, uint64_t batch)
+{
+    if (!h)
+        return RA_EINVAL;
+    auto it = h->batches.find(batch);
+    if (it == h->batches.end())
+        return RA_EINVAL;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (auto &tk : h->tickets)
+        if (tk.second.batch == batch)
+            tk.second.batch = ~0ull;  // results no longer available
+    free_batch(h, it->second);
+    h->batches.erase(it);
+    return RA_OK;
+}
+
+extern "C" int rawalign_dtw_submit_batch(rawalign_dtw_t *h, const float *events, const uint64_t *read_offsets,
+                                         uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
+                                         uint64_t *ticket)
+{
+    if (!ticket)
+        return RA_EINVAL;
+    uint64_t bid = 0;
+    int rc = rawalign_dtw_prepare_batch(h, events, read_offsets, n_reads, cands, n_cands, &bid);
+    if (rc != RA_OK)
+        return rc;
+    Batch &b = h->batches[bid];
+    b.auto_release = true;
+    rc = record_run(h, b);
+    if (rc != RA_OK) {
+        rawalign_dtw_release_batch(h, bid);
+        return rc;
+    }
+    b.ran = true;
+    return new_ticket(h, bid, b, ticket);
+}
+
+extern "C" int rawalign_dtw_poll(rawalign_dtw_t *h, uint64_t ticket, rawalign_result_t *out, uint32_t cap,
+                                 uint32_t *n_out, int64_t timeout_us)
+{
+    if (!h || !n_out || (cap && !out))
+        return RA_EINVAL;
+    *n_out = 0;
+    auto it = h->tickets.find(ticket);
+    if (it == h->tickets.end())
+        return RA_EINVAL;
+    cudaSetDevice(h->device);
+    Ticket &t = it->second;
+    auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        cudaError_t e = cudaEventQuery(t.done);
+        if (e == cudaSuccess)
+            break;
+        if (e != cudaErrorNotReady)
+            return cuda_ok(e);
+        if (timeout_us == 0)
+            return RA_ENOTREADY;
+        if (timeout_us > 0) {
+            auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0);
+            if (el.count() >= timeout_us)
+                return RA_ENOTREADY;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    int rc = RA_OK;
+    if (t.serving) {
+        uint32_t n = std::min<uint32_t>(cap, (uint32_t)t.host.size());
+        if (n)
+            memcpy(out, t.host.data(), sizeof(rawalign_result_t) * n);
+        *n_out = n;
+    } else {
+        if (t.batch == ~0ull)
+            rc = RA_EINVAL;
+        else {
+            int err[2] = {0, 0};
+            RA_CUDA(cudaMemcpy(err, t.d_err, sizeof(err), cudaMemcpyDeviceToHost));
+            if (err[1])
+                rc = RA_EINVAL;
+            uint32_t n = std::min<uint32_t>(cap, t.n);
+            if (n && rc == RA_OK)
+                RA_CUDA(cudaMemcpy(out, t.d_results, sizeof(rawalign_result_t) * n, cudaMemcpyDeviceToHost));
+            *n_out = rc == RA_OK ? n : 0;
+        }
+    }
+    cudaEventDestroy(t.done);
+    uint64_t bid = t.batch;
+    bool serving = t.serving;
+    h->tickets.erase(it);
+    if (!serving && bid != ~0ull) {
+        auto bt = h->batches.find(bid);
+        if (bt != h->batches.end() && bt->second.auto_release) {
+            free_batch(h, bt->second);
+            h->batches.erase(bt);
+        }
+    }
+    return rc;
+}
+
+extern "C" int rawalign_dtw_batch_stats(rawalign_dtw_t *h, uint64_t batch, rawalign_dtw_stats_t *out)
+{
+    if (!h || !out)
+        return RA_EINVAL;
+    auto it = h->batches.find(batch);
+    if (it == h->batches.end() || !it->second.ran)
+        return RA_EINVAL;
+    Batch &b = it->second;
+    float ms = 0, tot = 0;
+    RA_CUDA(cudaEventSynchronize(b.ev[3]));
+    if (b.cells == 0 && b.n_cands) {
+        std::vector<rawalign_result_t> res(b.n_cands);
+        RA_CUDA(cudaMemcpy(res.data(), b.d_results, sizeof(rawalign_result_t) * b.n_cands, cudaMemcpyDeviceToHost));
+        for (auto &r : res)
+            b.cells += r.cells;
+    }
+    RA_CUDA(cudaEventElapsedTime(&ms, b.ev[1], b.ev[2]));
+    RA_CUDA(cudaEventElapsedTime(&tot, b.ev[0], b.ev[3]));
+    out->dtw_ms = ms;
+    out->total_ms = tot;
+    out->cells = b.cells;
+    out->launches = b.launches;
+    out->pad = 0;
+    return RA_OK;
+}
+
+extern "C" uint64_t rawalign_dtw_batch_bytes(uint64_t n_events, uint32_t n_reads, uint32_t n_cands,
+                                             uint64_t total_ref_values)
+{
+    uint64_t b = 0;
+    auto add = [&](uint64_t x) { b += (x + 255) & ~255ull; };
+    add(4 * n_events);
+    add(sizeof(SigDesc) * (uint64_t)n_cands);
+    add(4 * total_ref_values);
+    add(sizeof(WorkDesc) * (uint64_t)n_cands);
+    add(sizeof(rawalign_result_t) * (uint64_t)n_cands);
+    add(8ull * n_reads);
+    add(4ull * n_cands);
+    add(256);
+    return b + (64ull << 20);  // ring buffers and slack
+}
+
+extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
+{
+    if (!h)
+        return RA_EINVAL;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (auto &tk : h->tickets)
+        if (tk.second.done)
+            cudaEventDestroy(tk.second.done);
+    for (auto &b : h->batches)
+        free_batch(h, b.second);
+    delete h;
+    return RA_OK;
+}
+
+// Serving entry points are defined in serve.cu.

@@ -1,0 +1,82 @@
+// internal.cuh -- device-side records shared by the kernels and the host engine
+// of librawalign_dtw (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rawalign_dtw.h"
+
+namespace ra {
+
+constexpr float kInf = __builtin_huge_valf();
+constexpr int kBigCol = 0x3FFFFFFF;  // column index no band reaches: masks a row off
+
+// One alignment, or one chunk of rows of one alignment (serving).
+// Rows are read events (global index row0 .. row0+nrows-1); columns are the
+// candidate's expected values 0..m-1; the band is |j*den - i*num| <= w*den
+// with global row index i (Sec. 2.4.3).
+struct WorkDesc {
+    uint64_t ev_off;    // index in the events array of row row0
+    uint64_t r_off;     // index in r_all of column 0
+    uint64_t fin_off;   // frontier store index of the row above row0 (its first band column)
+    uint64_t fout_off;  // frontier store index for the last row (serving)
+    int64_t num, den;   // band slope (unbanded: 0, 1 with w = m)
+    int32_t row0;       // first row (global index)
+    int32_t nrows;      // rows in this piece
+    int32_t m;          // columns
+    int32_t w;          // band half-width w_eff (>= 1)
+    int32_t cand;       // result slot (candidate index)
+    int32_t read;       // read slot for the per-read best
+    int32_t n_read;     // N_Read for the score
+    int32_t fin_lo;     // first column of the stored row above (row0-1); -1 = virtual start
+    int32_t fin_wid;    // stored columns - 1 (0 with the virtual start)
+    int32_t fout_lo;    // first column of the last row's band (serving)
+    int32_t dC;         // stripe period (steps between a lane's stripes)
+    int32_t w_report;   // w_eff reported in the result (-1 = no band)
+    int32_t a0;         // first in-band column of row0
+    int32_t s_end;      // steps until the group is done (<= 0: no in-band cell)
+    int32_t pad0, pad1;
+};
+static_assert(sizeof(WorkDesc) == 112, "WorkDesc layout");
+
+// Per-candidate description for the expected-signal step.
+struct SigDesc {
+    uint64_t ref_off;   // first base in the reference
+    uint64_t r_off;     // first output value in r_all
+    uint32_t len;       // bases in the region
+    uint32_t strand;    // 1 = reverse complement
+};
+
+struct StripeParams {
+    const WorkDesc *work;
+    int n_work;
+    int *queue;                    // next work item (atomic counter)
+    const float *events;
+    const float *r_all;
+    const float *fstore;           // frontier store (rows above row0)
+    float *fstore_out;             // frontier store for the last rows (serving)
+    rawalign_result_t *results;
+    unsigned long long *best_keys; // per read: (ordered score << 32) | ~cand
+    float *gring;                  // global ring buffers when not in shared memory
+    int ring_cap;                  // power of two, floats per group
+    int ring_in_smem;
+    float b_match;
+    int end_free;                  // 1: FREE end (min over the last row)
+    int *err;                      // error word (first failing work item + 1)
+};
+
+// Host-side launchers (dtw_kernels.cu).
+cudaError_t launch_expected_signal(const SigDesc *d, int n, const uint8_t *ref2bit, const float *pore,
+                                   int k, float *r_all, cudaStream_t s);
+cudaError_t launch_check_events(const float *ev, uint64_t n, int *err, cudaStream_t s);
+cudaError_t launch_stripe(int G, int HR, const StripeParams &p, int grid, int block, size_t smem,
+                          cudaStream_t s);
+int stripe_max_blocks_per_sm(int G, int HR, int block, size_t smem);
+cudaError_t launch_plain(const WorkDesc *w, const float *events, const float *r_all, float *diag,
+                         rawalign_result_t *results, unsigned long long *best_keys, float b_match,
+                         int end_free, cudaStream_t s);
+cudaError_t launch_decide(rawalign_result_t *results, int n, const unsigned long long *best_keys,
+                          const int *read_of, float thr, int final_decision, cudaStream_t s);
+
+}  // namespace ra

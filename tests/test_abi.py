@@ -1,0 +1,118 @@
+"""CPU-only checks of the boundary: the library builds, loads, and exports
+every entry point the public header declares; the record layouts seen by C,
+by the ctypes binding, by the input generator and by the oracle agree."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2310_05037_gb300 import binding as B
+from paper_2310_05037_gb300 import build as BUILD
+from paper_2310_05037_gb300 import synth as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rawalign_dtw.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    BUILD.build()
+    return B.load()
+
+
+def declared_symbols():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(rawalign_dtw_\w+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("rawalign_dtw_create", "rawalign_dtw_submit_batch", "rawalign_dtw_submit_chunk",
+              "rawalign_dtw_poll", "rawalign_dtw_destroy"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(rawalign_dtw_\w+)$", out, re.M))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    for s in declared_symbols():
+        assert s in B.SIGNATURES, s
+        getattr(lib, s)
+
+
+def _c_layout():
+    src = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "rawalign_dtw.h"
+#define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("cand %zu\nres %zu\ncfg %zu\nstats %zu\n", sizeof(rawalign_candidate_t), sizeof(rawalign_result_t),
+         sizeof(rawalign_dtw_config_t), sizeof(rawalign_dtw_stats_t));
+  O(rawalign_candidate_t, read_id); O(rawalign_candidate_t, ref_offset); O(rawalign_candidate_t, ref_len_bases);
+  O(rawalign_candidate_t, strand); O(rawalign_candidate_t, band_w); O(rawalign_candidate_t, slope_num);
+  O(rawalign_candidate_t, slope_den);
+  O(rawalign_result_t, cand_idx); O(rawalign_result_t, cost); O(rawalign_result_t, score); O(rawalign_result_t, end_i);
+  O(rawalign_result_t, end_j); O(rawalign_result_t, w_eff); O(rawalign_result_t, cells); O(rawalign_result_t, status);
+  O(rawalign_result_t, is_best); O(rawalign_result_t, decision);
+  O(rawalign_dtw_config_t, arena_dev); O(rawalign_dtw_config_t, arena_bytes); O(rawalign_dtw_config_t, cuda_stream);
+  O(rawalign_dtw_config_t, max_candidates); O(rawalign_dtw_config_t, kernel); O(rawalign_dtw_config_t, autotune_path);
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe])
+        lines = subprocess.check_output([exe], text=True).split("\n")
+    return dict(l.split() for l in lines if l.strip())
+
+
+def test_record_layouts_agree():
+    lay = _c_layout()
+    assert int(lay["cand"]) == C.sizeof(B.Candidate) == S.CANDIDATE_DTYPE.itemsize == C.sizeof(O.Candidate) == 48
+    assert int(lay["res"]) == C.sizeof(B.Result) == B.RESULT_DTYPE.itemsize == 56
+    assert int(lay["cfg"]) == C.sizeof(B.Config)
+    assert int(lay["stats"]) == C.sizeof(B.Stats)
+    for k, v in lay.items():
+        if "." not in k:
+            continue
+        T, f = k.split(".")
+        py = {"rawalign_candidate_t": B.Candidate, "rawalign_result_t": B.Result, "rawalign_dtw_config_t": B.Config}[T]
+        assert getattr(py, f).offset == int(v), k
+        if T == "rawalign_candidate_t":
+            assert S.CANDIDATE_DTYPE.fields[f][1] == int(v), k
+            assert getattr(O.Candidate, f).offset == int(v), k
+        if T == "rawalign_result_t":
+            assert getattr(O.Result, f).offset == int(v), k
+
+
+def test_product_path_does_not_reach_the_oracle():
+    """The package never imports or links the oracle."""
+    pkg = os.path.join(ROOT, "paper_2310_05037_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "rawalign_oracle" not in txt and "liboracle" not in txt, f
+    out = subprocess.run(["ldd", B.LIB_PATH], capture_output=True, text=True).stdout if os.path.exists(B.LIB_PATH) else ""
+    assert "oracle" not in out
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    saved = B._lib
+    try:
+        B._lib = None
+        with pytest.raises(RuntimeError):
+            B.load(str(tmp_path / "nope.so"))
+    finally:
+        B._lib = saved
