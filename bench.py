@@ -1,0 +1,362 @@
+"""Benchmark of the RawAlign DTW alignment path on GB300.
+
+One step = one pass of the whole path over the batched-uneven workload
+(20k reads with lognormal event counts, 1-8 candidate regions each on a
+100 Mb reference, band 10 % of the span): expected signal, band, DTW, end
+cell, score and per-read decision, all in the library's kernels (one CUDA
+graph replay).  Inputs are resident in HBM when the timed region starts and
+are larger than L2; L2 is also flushed between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  value = in-band DTW cells / device time
+(GCUPS, whole job over all ranks).  e2e = the same metric through the public
+submit/poll calls from pinned host buffers (copies included).  Extra keys:
+reads_per_s, the plain one-alignment-per-launch kernel on a sample of the same
+workload, and the batched/plain speed-up.  --impl reference times the CPU
+oracle (the only reference this path has) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("batched_uneven: 20000 reads, lognormal event counts (median 1500, 200-8000), 1-8 candidates "
+            "per read (1 true + decoys) on a 100 Mb uniform-ACGT reference, span = events x U(0.9,1.3), "
+            "band 10% of span, 6-mer pore table N(0,1), noise sd 0.3, 5% skips, FP32 global DTW")
+METRIC = "DTW GCUPS and reads/s (batched and served vs plain per-alignment kernel); p50/p99 chunk latency"
+OPS_PER_CELL = 4  # sub, min, min, add per DP cell
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[4], f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        pmax = max(r[2] for r in rows)
+        load = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in load:
+            for nm, v in zip(names, r[4:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(load), "power_w_max": pmax}
+
+
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if n_gpus > 0 else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(w, seconds=15.0, seed=1):
+    """The oracle, as it stands, single-threaded on the host: a random sample
+    of the workload's alignments, about `seconds` of CPU work."""
+    import oracle as O
+
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(w.n_cands)
+    cells = 0
+    done = 0
+    t0 = time.perf_counter()
+    chunk = 16
+    pos = 0
+    while time.perf_counter() - t0 < seconds and pos < len(order):
+        sub = w.subset(np.sort(order[pos : pos + chunk]))
+        pos += chunk
+        res = O.map_batch(sub.k, sub.b_match, sub.score_threshold, sub.end_mode, sub.pore, sub.ref2bit,
+                          sub.ref_len, sub.events, sub.read_offsets, sub.cands)
+        cells += int(res["cells"].sum())
+        done += len(res)
+    el = time.perf_counter() - t0
+    return {"value": cells / el / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d random alignments of the workload (%.3g in-band cells) in %.1f s, single thread"
+                      % (done, cells, el), "seconds": el}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--reads", type=int, default=20000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    from paper_2310_05037_gb300 import synth as S
+
+    if args.impl == "reference":
+        return run_reference(args, S)
+
+    world, rank, local = dist_init(args.gpus)
+    import torch
+
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2310_05037_gb300 import binding as B
+
+    w = S.config_batched(n_reads=args.reads, seed=0x5EED0002 + rank)
+    m_total = int(np.sum(w.cands["ref_len_bases"].astype(np.int64) - w.k + 1))
+    need = B.rawalign_dtw_batch_bytes(len(w.events), w.n_reads, w.n_cands, m_total)
+    arena = 2 * need + len(w.ref2bit) + (256 << 20)
+    al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena, device="cuda:%d" % local)
+    stream = al.stream
+    batch = al.prepare(w.events, w.read_offsets, w.cands)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:%d" % local)
+
+    def one_step():
+        t = al.run(batch)
+        return t
+
+    for _ in range(args.warmup):
+        t = one_step()
+        res = al.poll(t, w.n_cands)
+    cells_step = int(res["cells"].sum())
+    reads_step = w.n_reads
+    launches_step = al.stats(batch).launches
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    dtw_ms = []
+    tot_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev0[i].record(stream)
+            t = one_step()
+            with torch.cuda.stream(stream):
+                ev1[i].record(stream)
+            al.poll(t, 0)
+            st = al.stats(batch)
+            dtw_ms.append(st.dtw_ms)
+            tot_ms.append(ev0[i].elapsed_time(ev1[i]))
+        torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.summary()
+    step_ms = sum(tot_ms) / len(tot_ms)
+    total_s = max_over_ranks(sum(tot_ms) / 1e3, world)
+    total_cells = sum_over_ranks(cells_step * args.steps, world)
+    value = total_cells / total_s / 1e9
+    dtw_avg_ms = sum(dtw_ms) / len(dtw_ms)
+
+    peaks = load_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_gcups = sms * 128 * f_max * 1e6 / OPS_PER_CELL / 1e9
+    achieved = cells_step / (dtw_avg_ms / 1e3) / 1e9
+    roofline = {
+        "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak_gcups, 1), "unit": "GCUPS",
+        "frac": round(achieved / peak_gcups, 4), "traffic": None,
+        "kernel": "dtw_stripe_kernel", "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / %d ops per cell "
+        "(derived, MEASURED_PEAKS sm_max_mhz)" % (sms, f_max, OPS_PER_CELL),
+    }
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = round(achieved / (peak_gcups * clocks["sm_mhz"] / f_max), 4)
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reads": w.n_reads, "alignments": w.n_cands, "cells_per_step": cells_step,
+                   "l2": "inputs larger than L2 (expected signal %.0f MB, events %.0f MB) and a 256 MB L2 flush "
+                         "between timed steps" % (m_total * 4 / 1e6, len(w.events) * 4 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "reads_per_s": round(sum_over_ranks(reads_step * args.steps, world) / total_s, 1),
+        "dtw_kernel_ms": round(dtw_avg_ms, 3),
+        "gpu_launches": int(launches_step * args.steps),
+        "roofline": roofline, "clocks": clocks,
+    }
+
+    # plain one-alignment-per-launch kernel on a sample of the same workload
+    if not args.no_plain and rank == 0:
+        rng = np.random.default_rng(5)
+        sub = w.subset(np.sort(rng.choice(w.n_cands, size=min(300, w.n_cands), replace=False)))
+        alp = B.Aligner(sub.pore, sub.ref2bit, sub.ref_len, arena_bytes=1 << 30, kernel=B.RA_KERNEL_PLAIN,
+                        device="cuda:%d" % local)
+        bp = alp.prepare(sub.events, sub.read_offsets, sub.cands)
+        tp = alp.run(bp)
+        rp = alp.poll(tp, sub.n_cands)
+        tp = alp.run(bp)
+        alp.poll(tp, 0)
+        stp = alp.stats(bp)
+        plain_gcups = float(rp["cells"].sum()) / (stp.dtw_ms / 1e3) / 1e9
+        alp.release(bp)
+        alp.close()
+        out["plain_kernel"] = {"gcups": round(plain_gcups, 3), "sample_alignments": sub.n_cands,
+                               "launches": int(stp.launches)}
+        out["speedup_vs_plain"] = round(achieved / plain_gcups, 1)
+
+    # end to end through submit/poll with pinned host buffers
+    if not args.no_e2e:
+        ev_h = torch.from_numpy(w.events).pin_memory()
+        off_h = torch.from_numpy(w.read_offsets.view(np.int64)).pin_memory()
+        cand_h = torch.from_numpy(w.cands.view(np.uint8)).pin_memory()
+        ev_np = ev_h.numpy()
+        off_np = off_h.numpy().view(np.uint64)
+        cand_np = cand_h.numpy().view(S.CANDIDATE_DTYPE)
+        for _ in range(2):
+            r = al.align(ev_np, off_np, cand_np)
+        barrier(world)
+        t0 = time.perf_counter()
+        e2e_steps = max(3, args.steps // 2)
+        for _ in range(e2e_steps):
+            r = al.align(ev_np, off_np, cand_np)
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        e2e_cells = sum_over_ranks(float(r["cells"].sum()) * e2e_steps, world)
+        out["e2e"] = {"value": round(e2e_cells / el / 1e9, 2), "unit": "GCUPS",
+                      "h2d_bytes_per_step": int(w.events.nbytes + w.read_offsets.nbytes + w.cands.nbytes),
+                      "d2h_bytes_per_step": int(w.n_cands * B.RESULT_DTYPE.itemsize),
+                      "ms_per_step": round(el / e2e_steps * 1e3, 2)}
+
+    if not args.no_cpu and rank == 0 and world >= 1:
+        cb = cpu_baseline(w, seconds=args.cpu_seconds)
+        cb["cores"] = 1
+        out["cpu_baseline"] = {k: v for k, v in cb.items() if k != "seconds"}
+
+    al.release(batch)
+    al.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_reference(args, S):
+    """The reference arm: the CPU oracle on bounded samples of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = S.config_batched(n_reads=args.reads)
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup):
+        cpu_baseline(w, seconds=per_step, seed=100 + i)
+    vals, secs, samples = [], [], []
+    for i in range(args.steps):
+        cb = cpu_baseline(w, seconds=per_step, seed=200 + i)
+        vals.append(cb["value"])
+        secs.append(cb["seconds"])
+        samples.append(cb["sample"])
+    value = statistics.mean(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GCUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(secs), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reads": w.n_reads, "alignments": w.n_cands},
+        "cpu_baseline": {"value": round(value, 5), "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                         "sample": "each step: random alignments of the workload for %.1f s, single thread; "
+                                   "last: %s" % (per_step, samples[-1])},
+        "e2e": {"value": round(value, 5), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -57,10 +57,10 @@ typedef enum {
 enum { RA_END_GLOBAL = 0, RA_END_FREE = 1 };            /* end of the DTW */
 enum { RA_UNMAPPED = 0, RA_MAPPED = 1, RA_PENDING = 2 };/* decision */
 /* kernel choice: AUTO picks a striped variant per alignment; PLAIN runs one
- * alignment per launch; STRIPE_G32..G4 force the striped variant with 32, 16,
- * 8 or 4 lanes per alignment (tuning and tests). */
-enum { RA_KERNEL_AUTO = 0, RA_KERNEL_PLAIN = 1, RA_KERNEL_STRIPE_G32 = 2, RA_KERNEL_STRIPE_G16 = 3,
-       RA_KERNEL_STRIPE_G8 = 4, RA_KERNEL_STRIPE_G4 = 5 };
+ * alignment per launch; RA_KERNEL_VARIANT0 + v forces striped variant v for
+ * every alignment (tuning and tests): v = 0..5 are (lanes per alignment, rows
+ * per lane) = (32,16) (16,16) (32,8) (16,8) (8,8) (4,8). */
+enum { RA_KERNEL_AUTO = 0, RA_KERNEL_PLAIN = 1, RA_KERNEL_VARIANT0 = 16 };
 
 typedef struct {
     int32_t k;                 /* k-mer length, 1..8; pore table has 4^k entries */

@@ -26,8 +26,11 @@ using namespace ra;
 namespace {
 
 constexpr int kBlock = 128;
-const int kVariants[][2] = {{32, 8}, {16, 8}, {8, 8}, {4, 8}};
-constexpr int kNumVariants = 4;
+// (lanes per alignment, rows per lane); the cost factor is the relative issue
+// cost of one lane-cell slot (more rows per lane amortise the per-step work).
+const int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}};
+const double kSlotCost[] = {1.0, 1.0, 1.25, 1.25, 1.25, 1.25};
+constexpr int kNumVariants = 6;
 
 // ---------------------------------------------------------------- band math
 inline int64_t fdiv(int64_t a, int64_t b)
@@ -171,6 +174,7 @@ struct Arena {
 
 struct ClassLaunch {
     int G = 0, HR = 0;
+    double max_cost = 0;       // lane-steps of the class's largest alignment
     int first = 0, count = 0;  // range in the sorted work array
     int ring_cap = 0;
     int ring_in_smem = 1;
@@ -198,7 +202,7 @@ struct Batch {
     uint64_t cells = 0;
     bool auto_release = false;
     bool plain = false;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph_part[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     uint32_t launches = 0;
     bool ran = false;
@@ -249,6 +253,8 @@ struct PendingChunk {
 struct rawalign_dtw {
     rawalign_dtw_config_t cfg{};
     cudaStream_t stream = nullptr;
+    cudaStream_t aux[kNumVariants] = {};   // one branch per kernel variant
+    cudaEvent_t fork = nullptr, join[kNumVariants] = {};
     int device = 0;
     int sm_count = 152;
     Arena arena;
@@ -309,8 +315,9 @@ int next_pow2(int64_t x)
 
 void free_batch(rawalign_dtw *h, Batch &b)
 {
-    if (b.graph)
-        cudaGraphExecDestroy(b.graph);
+    for (auto &g : b.graph_part)
+        if (g)
+            cudaGraphExecDestroy(g);
     for (auto &e : b.ev)
         if (e)
             cudaEventDestroy(e);
@@ -341,8 +348,8 @@ int choose_variant(const BandDef &band, int64_t n, Sched &out)
             out = s;
             return 0;
         }
-        // prefer wide groups unless they waste clearly more lane time
-        const double score = s.eff * (1.0 + 0.04 * (kNumVariants - v));
+        // cells per unit of issue cost; ties go to the earlier (wider) variant
+        const double score = s.eff / kSlotCost[v] * (1.0 + 0.02 * (kNumVariants - v));
         if (score > best_score) {
             best_score = score;
             best = v;
@@ -413,7 +420,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         wd.fin_wid = 0;
         wd.w_report = wrep;
         Sched s;
-        const int forced = h->cfg.kernel - RA_KERNEL_STRIPE_G32;
+        const int forced = h->cfg.kernel >= RA_KERNEL_VARIANT0 ? h->cfg.kernel - RA_KERNEL_VARIANT0 : -1;
         if (b.plain || (forced >= 0 && forced < kNumVariants)) {
             it.variant = b.plain ? 0 : forced;
             s = schedule(band, 0, n, kVariants[it.variant][0], kVariants[it.variant][1]);
@@ -482,9 +489,10 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
             cl.count = pos - cl.first;
             if (cl.count == 0)
                 continue;
+            cl.max_cost = items[order[cl.first]].cost;
             cl.ring_cap = next_pow2(need);
             const int groups_per_block = kBlock / cl.G;
-            size_t smem = (size_t)groups_per_block * cl.ring_cap * sizeof(float);
+            size_t smem = (size_t)groups_per_block * (cl.ring_cap + 1) * sizeof(float);
             cl.ring_in_smem = smem <= 64 * 1024;
             cl.smem = cl.ring_in_smem ? smem : 0;
             int nb = stripe_max_blocks_per_sm(cl.G, cl.HR, kBlock, cl.smem);
@@ -500,6 +508,9 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
             }
             b.classes.push_back(cl);
         }
+        // the class holding the longest alignments starts first
+        std::stable_sort(b.classes.begin(), b.classes.end(),
+                         [](const ClassLaunch &x, const ClassLaunch &y) { return x.max_cost > y.max_cost; });
     }
     cudaStream_t s = h->stream;
     RA_CUDA(cudaMemcpyAsync(b.d_events, events, sizeof(float) * b.n_events, cudaMemcpyHostToDevice, s));
@@ -513,76 +524,106 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     return RA_OK;
 }
 
-int record_run(rawalign_dtw *h, Batch &b)
+// The path in three parts: pre (reset, event check, expected signal), the DTW
+// kernels, post (decision).  Timing events sit between the parts, outside any
+// graph.
+int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
 {
     cudaStream_t s = h->stream;
-    uint32_t launches = 0;
-    RA_CUDA(cudaEventRecord(b.ev[0], s));
-    RA_CUDA(cudaMemsetAsync(b.d_keys, 0, sizeof(unsigned long long) * std::max<uint32_t>(b.n_reads, 1), s));
-    RA_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int) * (kNumVariants + 2), s));
-    RA_CUDA(launch_check_events(b.d_events, b.n_events, b.d_err, s));
-    launches += b.n_events ? 1 : 0;
-    RA_CUDA(launch_expected_signal(b.d_sig, (int)b.n_cands, h->d_ref, h->d_pore, h->cfg.k, b.d_r, s));
-    launches += b.n_cands ? 1 : 0;
-    RA_CUDA(cudaEventRecord(b.ev[1], s));
-    if (b.plain) {
-        for (uint32_t c = 0; c < b.n_cands; ++c) {
-            RA_CUDA(launch_plain(b.d_work + c, b.d_events, b.d_r, b.d_plain_diag, b.d_results, b.d_keys,
-                                 h->cfg.b_match, h->cfg.end_mode == RA_END_FREE, s));
-            ++launches;
+    if (part == 0) {
+        RA_CUDA(cudaMemsetAsync(b.d_keys, 0, sizeof(unsigned long long) * std::max<uint32_t>(b.n_reads, 1), s));
+        RA_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int) * (kNumVariants + 2), s));
+        RA_CUDA(launch_check_events(b.d_events, b.n_events, b.d_err, s));
+        launches += b.n_events ? 1 : 0;
+        RA_CUDA(launch_expected_signal(b.d_sig, (int)b.n_cands, h->d_ref, h->d_pore, h->cfg.k, b.d_r, s));
+        launches += b.n_cands ? 1 : 0;
+    } else if (part == 1) {
+        if (b.plain) {
+            for (uint32_t c = 0; c < b.n_cands; ++c) {
+                RA_CUDA(launch_plain(b.d_work + c, b.d_events, b.d_r, b.d_plain_diag, b.d_results, b.d_keys,
+                                     h->cfg.b_match, h->cfg.end_mode == RA_END_FREE, s));
+                ++launches;
+            }
+        } else {
+            // variant classes run as parallel branches: a class whose queue
+            // drains early leaves its SMs to the classes still running
+            RA_CUDA(cudaEventRecord(h->fork, s));
+            int qi = 0;
+            for (size_t ci = 0; ci < b.classes.size(); ++ci) {
+                auto &cl = b.classes[ci];
+                cudaStream_t cs = h->aux[ci];
+                RA_CUDA(cudaStreamWaitEvent(cs, h->fork, 0));
+                StripeParams p{};
+                p.work = b.d_work + cl.first;
+                p.n_work = cl.count;
+                p.queue = b.d_queue + (qi++);
+                p.events = b.d_events;
+                p.r_all = b.d_r;
+                p.fstore = nullptr;
+                p.fstore_out = nullptr;
+                p.results = b.d_results;
+                p.best_keys = b.d_keys;
+                p.gring = cl.gring;
+                p.ring_cap = cl.ring_cap;
+                p.ring_in_smem = cl.ring_in_smem;
+                p.b_match = h->cfg.b_match;
+                p.end_free = h->cfg.end_mode == RA_END_FREE;
+                p.err = b.d_err;
+                RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
+                ++launches;
+                RA_CUDA(cudaEventRecord(h->join[ci], cs));
+                RA_CUDA(cudaStreamWaitEvent(s, h->join[ci], 0));
+            }
         }
     } else {
-        int qi = 0;
-        for (auto &cl : b.classes) {
-            StripeParams p{};
-            p.work = b.d_work + cl.first;
-            p.n_work = cl.count;
-            p.queue = b.d_queue + (qi++);
-            p.events = b.d_events;
-            p.r_all = b.d_r;
-            p.fstore = nullptr;
-            p.fstore_out = nullptr;
-            p.results = b.d_results;
-            p.best_keys = b.d_keys;
-            p.gring = cl.gring;
-            p.ring_cap = cl.ring_cap;
-            p.ring_in_smem = cl.ring_in_smem;
-            p.b_match = h->cfg.b_match;
-            p.end_free = h->cfg.end_mode == RA_END_FREE;
-            p.err = b.d_err;
-            RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, s));
-            ++launches;
-        }
+        RA_CUDA(launch_decide(b.d_results, (int)b.n_cands, b.d_keys, b.d_read_of, h->cfg.score_threshold, 1, s));
+        launches += b.n_cands ? 1 : 0;
     }
-    RA_CUDA(cudaEventRecord(b.ev[2], s));
-    RA_CUDA(launch_decide(b.d_results, (int)b.n_cands, b.d_keys, b.d_read_of, h->cfg.score_threshold, 1, s));
-    launches += b.n_cands ? 1 : 0;
-    RA_CUDA(cudaEventRecord(b.ev[3], s));
+    return RA_OK;
+}
+
+int record_run(rawalign_dtw *h, Batch &b)
+{
+    uint32_t launches = 0;
+    for (int part = 0; part < 3; ++part) {
+        RA_CUDA(cudaEventRecord(b.ev[part], h->stream));
+        int rc = record_part(h, b, part, launches);
+        if (rc != RA_OK)
+            return rc;
+    }
+    RA_CUDA(cudaEventRecord(b.ev[3], h->stream));
     b.launches = launches;
     return RA_OK;
 }
 
 int run_batch(rawalign_dtw *h, Batch &b)
 {
-    if (b.plain) {
+    if (b.plain)
         return record_run(h, b);
-    }
-    if (!b.graph) {
-        cudaGraph_t g = nullptr;
-        RA_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        int rc = record_run(h, b);
-        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-        if (rc != RA_OK) {
-            if (g)
-                cudaGraphDestroy(g);
-            return rc;
+    if (!b.graph_part[0]) {
+        uint32_t launches = 0;
+        for (int part = 0; part < 3; ++part) {
+            cudaGraph_t g = nullptr;
+            RA_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            int rc = record_part(h, b, part, launches);
+            cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+            if (rc != RA_OK) {
+                if (g)
+                    cudaGraphDestroy(g);
+                return rc;
+            }
+            RA_CUDA(e);
+            e = cudaGraphInstantiate(&b.graph_part[part], g, 0);
+            cudaGraphDestroy(g);
+            RA_CUDA(e);
         }
-        RA_CUDA(e);
-        e = cudaGraphInstantiate(&b.graph, g, 0);
-        cudaGraphDestroy(g);
-        RA_CUDA(e);
+        b.launches = launches;
     }
-    RA_CUDA(cudaGraphLaunch(b.graph, h->stream));
+    for (int part = 0; part < 3; ++part) {
+        RA_CUDA(cudaEventRecord(b.ev[part], h->stream));
+        RA_CUDA(cudaGraphLaunch(b.graph_part[part], h->stream));
+    }
+    RA_CUDA(cudaEventRecord(b.ev[3], h->stream));
     return RA_OK;
 }
 
@@ -618,7 +659,8 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
         return RA_EINVAL;
     if (config->end_mode != RA_END_GLOBAL && config->end_mode != RA_END_FREE)
         return RA_EINVAL;
-    if (config->kernel < RA_KERNEL_AUTO || config->kernel > RA_KERNEL_STRIPE_G4)
+    if (config->kernel < RA_KERNEL_AUTO || config->kernel == 2 || config->kernel == 3 ||
+        config->kernel >= RA_KERNEL_VARIANT0 + kNumVariants)
         return RA_EINVAL;
     const uint64_t n_pore = 1ull << (2 * config->k);
     for (uint64_t x = 0; x < n_pore; ++x)
@@ -629,9 +671,22 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
         return RA_ENOMEM;
     h->cfg = *config;
     h->cfg.autotune_path = nullptr;
+    if (const char *mm = getenv("RAWALIGN_MASK_MODE"))
+        set_mask_mode(strcmp(mm, "rowcmp") == 0 ? 0 : 1);
     h->stream = (cudaStream_t)config->cuda_stream;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (cudaStreamCreateWithFlags(&h->aux[v], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->join[v], cudaEventDisableTiming) != cudaSuccess) {
+            delete h;
+            return RA_EDEVICE;
+        }
+    }
+    if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) {
+        delete h;
+        return RA_EDEVICE;
+    }
     h->arena.init(config->arena_dev, config->arena_bytes);
     h->d_pore = (float *)h->arena.alloc(sizeof(float) * n_pore);
     h->d_ref = (uint8_t *)h->arena.alloc(std::max<uint64_t>((ref_len + 3) / 4, 1));
@@ -841,6 +896,14 @@ extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
             cudaEventDestroy(tk.second.done);
     for (auto &b : h->batches)
         free_batch(h, b.second);
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (h->aux[v])
+            cudaStreamDestroy(h->aux[v]);
+        if (h->join[v])
+            cudaEventDestroy(h->join[v]);
+    }
+    if (h->fork)
+        cudaEventDestroy(h->fork);
     delete h;
     return RA_OK;
 }

@@ -14,8 +14,7 @@ from gpu_util import assert_bit_exact, edge_workload, run_gpu, run_oracle, tiny_
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [B.RA_KERNEL_AUTO, B.RA_KERNEL_STRIPE[32], B.RA_KERNEL_STRIPE[16], B.RA_KERNEL_STRIPE[8],
-            B.RA_KERNEL_STRIPE[4]]
+VARIANTS = [B.RA_KERNEL_AUTO] + [B.RA_KERNEL_STRIPE[gh] for gh in B.VARIANTS]
 
 
 @pytest.fixture(scope="module", autouse=True)
