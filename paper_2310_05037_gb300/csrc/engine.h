@@ -1,0 +1,296 @@
+// engine.h -- host-side planning types shared by engine.cu (batches) and
+// serve.cu (Read-Until serving): band rule, stripe schedule, arena, records,
+// and the handle itself.  Internal to librawalign_dtw.
+#pragma once
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace ra;
+
+namespace ra_host {
+
+constexpr int kBlock = 128;
+// (lanes per alignment, rows per lane); the cost factor is the relative issue
+// cost of one lane-cell slot (more rows per lane amortise the per-step work).
+const int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}};
+const double kSlotCost[] = {1.0, 1.0, 1.25, 1.25, 1.25, 1.25};
+constexpr int kNumVariants = 6;
+
+// ---------------------------------------------------------------- band math
+inline int64_t fdiv(int64_t a, int64_t b)
+{
+    int64_t q = a / b, r = a % b;
+    return (r != 0 && ((r < 0) != (b < 0))) ? q - 1 : q;
+}
+inline int64_t cdiv(int64_t a, int64_t b) { return -fdiv(-a, b); }
+
+struct BandDef {
+    int64_t num = 0, den = 1, w = 0, m = 1;
+    int64_t lo(int64_t i) const { return std::max<int64_t>(0, cdiv(i * num - w * den, den)); }
+    int64_t hi(int64_t i) const { return std::min<int64_t>(m - 1, fdiv(i * num + w * den, den)); }
+};
+
+// Band of one candidate (Sec. 2.4.3): derived slope (m-1)/(n-1) unless given;
+// w_eff = max(w, ceil(num/(2 den)), 1); no band -> num 0, den 1, w = m.
+inline int band_for(int64_t n, int64_t m, int32_t band_w, int64_t num_in, int64_t den_in, BandDef &b,
+             int32_t &w_report)
+{
+    b.m = m;
+    if (band_w < 0 || n == 1 || m == 1) {
+        b.num = 0;
+        b.den = 1;
+        b.w = m;
+        w_report = -1;
+        return 0;
+    }
+    int64_t num = num_in, den = den_in;
+    if (num == 0 && den == 0) {
+        num = m - 1;
+        den = n - 1;
+    }
+    if (num < 0 || den <= 0 || num > (1ll << 30) || den > (1ll << 30))
+        return -1;
+    int64_t half = (num + 2 * den - 1) / (2 * den);
+    int64_t w = std::max<int64_t>(std::max<int64_t>(band_w, half), 1);
+    if (w > (1ll << 30))
+        return -1;
+    b.num = num;
+    b.den = den;
+    b.w = w;
+    w_report = (int32_t)w;
+    return 0;
+}
+
+// Schedule of one piece (rows row0..row0+nrows-1) for a (G, HR) variant, in
+// O(1): dC bounds b(k,t) - a(k+1,t) + 2 for every lane and stripe, where b is
+// the last in-band column of a lane's rows in stripe k and a the first of its
+// rows in stripe k+1.  With hi(x) <= x*s + w and lo(y) >= y*s - w
+// (s = num/den, y - x = H - HR + 1): b - a <= 2w - (H - HR + 1) s, and
+// b - a <= m - 1 from the table's edges.
+struct Sched {
+    int32_t dC = 0, a0 = 0, s_end = 0;
+    double cells_est = 0;
+    double eff = 0;  // in-band cells / lane-cell slots (estimate)
+};
+
+inline Sched schedule(const BandDef &b, int64_t row0, int64_t nrows, int G, int HR)
+{
+    Sched s;
+    const int64_t H = (int64_t)G * HR;
+    const int64_t K = (nrows + H - 1) / H;
+    const int64_t last = row0 + nrows - 1;
+    s.a0 = (int32_t)b.lo(row0);
+    if (s.a0 > b.m - 1) {
+        s.s_end = 0;
+        return s;
+    }
+    int64_t span = fdiv(2 * b.w * b.den - (H - HR + 1) * b.num, b.den);
+    span = std::min<int64_t>(span, b.m - 1);
+    const int64_t dC = std::max<int64_t>(G + 1, span + 2);
+    const int64_t nl = nrows - 1 - (K - 1) * H;
+    const int64_t t_last = nl / HR;
+    const int64_t b_last = b.hi(last);
+    s.dC = (int32_t)dC;
+    const int64_t se = b_last - s.a0 + 3 + t_last + (K - 1) * dC;
+    s.s_end = (int32_t)std::max<int64_t>(se, 1);
+    s.cells_est = (double)nrows * (double)std::min<int64_t>(2 * b.w + 1, b.m);
+    const double slots = (double)s.s_end * G * HR;
+    s.eff = slots > 0 ? s.cells_est / slots : 0;
+    return s;
+}
+
+// ---------------------------------------------------------------- arena
+struct Arena {
+    char *base = nullptr;
+    uint64_t size = 0;
+    std::map<uint64_t, uint64_t> free_;  // offset -> size
+    void init(void *p, uint64_t n)
+    {
+        base = (char *)p;
+        size = n;
+        free_.clear();
+        if (n)
+            free_[0] = n;
+    }
+    void *alloc(uint64_t n)
+    {
+        n = (n + 255) & ~255ull;
+        if (n == 0)
+            n = 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                uint64_t off = it->first, sz = it->second;
+                free_.erase(it);
+                if (sz > n)
+                    free_[off + n] = sz - n;
+                used_[off] = n;
+                return base + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(void *p)
+    {
+        if (!p)
+            return;
+        uint64_t off = (uint64_t)((char *)p - base);
+        auto u = used_.find(off);
+        if (u == used_.end())
+            return;
+        uint64_t n = u->second;
+        used_.erase(u);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    std::map<uint64_t, uint64_t> used_;
+};
+
+struct ClassLaunch {
+    int G = 0, HR = 0;
+    double max_cost = 0;       // lane-steps of the class's largest alignment
+    int first = 0, count = 0;  // range in the sorted work array
+    int ring_cap = 0;
+    int ring_in_smem = 1;
+    int grid = 0;
+    size_t smem = 0;
+    float *gring = nullptr;
+};
+
+struct Batch {
+    uint32_t n_reads = 0, n_cands = 0;
+    uint64_t n_events = 0;
+    std::vector<void *> blocks;  // arena allocations
+    float *d_events = nullptr;
+    SigDesc *d_sig = nullptr;
+    float *d_r = nullptr;
+    WorkDesc *d_work = nullptr;
+    rawalign_result_t *d_results = nullptr;
+    unsigned long long *d_keys = nullptr;
+    int *d_read_of = nullptr;
+    int *d_queue = nullptr;  // [kNumVariants]
+    int *d_err = nullptr;    // [2]
+    float *d_plain_diag = nullptr;
+    int max_rows = 0;
+    std::vector<ClassLaunch> classes;
+    uint64_t cells = 0;
+    bool auto_release = false;
+    bool plain = false;
+    cudaGraphExec_t graph_part[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t launches = 0;
+    bool ran = false;
+};
+
+struct Ticket {
+    uint64_t batch = 0;  // batch id (0 = serving)
+    cudaEvent_t done = nullptr;
+    rawalign_result_t *d_results = nullptr;
+    uint32_t n = 0;
+    int *d_err = nullptr;
+    std::vector<rawalign_result_t> host;  // serving: filled at flush completion
+    std::vector<uint64_t> read_ids;       // serving: caller read ids per result
+    bool serving = false;
+};
+
+struct ServeState;
+
+}  // namespace ra_host
+
+using namespace ra_host;
+
+struct rawalign_dtw {
+    rawalign_dtw_config_t cfg{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t aux[kNumVariants] = {};   // one branch per kernel variant
+    cudaEvent_t fork = nullptr, join[kNumVariants] = {};
+    int device = 0;
+    int sm_count = 152;
+    Arena arena;
+    float *d_pore = nullptr;
+    uint8_t *d_ref = nullptr;
+    uint64_t ref_len = 0;
+    uint64_t next_id = 1;
+    std::map<uint64_t, Batch> batches;
+    std::map<uint64_t, Ticket> tickets;
+    int max_blocks[kNumVariants][2] = {};
+    ServeState *serve = nullptr;       // Read-Until serving state (serve.cu)
+};
+
+
+namespace ra_host {
+
+inline int cuda_ok(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return RA_OK;
+    fprintf(stderr, "rawalign_dtw: CUDA error %s\n", cudaGetErrorString(e));
+    return RA_EDEVICE;
+}
+
+#define RA_CUDA(x)                      \
+    do {                                \
+        int rc__ = ra_host::cuda_ok(x); \
+        if (rc__ != RA_OK)              \
+            return rc__;                \
+    } while (0)
+
+inline int next_pow2(int64_t x)
+{
+    int64_t p = 1;
+    while (p < x)
+        p <<= 1;
+    return (int)p;
+}
+
+// Chooses the striped variant for one piece of an alignment: most in-band
+// cells per unit of issue cost, ties to the earlier (wider) variant.
+inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &out)
+{
+    int best = -1;
+    double best_score = -1;
+    for (int v = 0; v < kNumVariants; ++v) {
+        const int G = kVariants[v][0], HR = kVariants[v][1];
+        Sched s = schedule(band, row0, n, G, HR);
+        if (s.s_end <= 0) {
+            out = s;
+            return 0;
+        }
+        const double score = s.eff / kSlotCost[v] * (1.0 + 0.02 * (kNumVariants - v));
+        if (score > best_score) {
+            best_score = score;
+            best = v;
+            out = s;
+        }
+    }
+    return best;
+}
+
+// serving entry points' helpers (serve.cu)
+void serve_destroy(rawalign_dtw *h);
+int serve_poll(rawalign_dtw *h, uint64_t ticket, rawalign_result_t *out, uint32_t cap, uint32_t *n_out,
+               int64_t timeout_us, bool *handled);
+
+}  // namespace ra_host
