@@ -179,6 +179,31 @@ typedef struct {
 } rawalign_dtw_stats_t;
 int rawalign_dtw_batch_stats(rawalign_dtw_t *h, uint64_t batch, rawalign_dtw_stats_t *out);
 
+/* One alignment that allocates nothing (the paper has no counterpart to this
+ * call; it exists for deployment).  Some callers may not allocate device
+ * memory at all: a plug-in inside a host program that owns the whole device
+ * memory budget, or a control loop that must never call cudaMalloc because it
+ * can wait on the device and stall the process's other streams.  Such a
+ * caller passes device pointers it already owns: d_events (n_events floats),
+ * d_ref_signal (m expected values, i.e. the pore means of the region's
+ * k-mers) and d_result (one rawalign_result_t, written on the stream).  The
+ * band, end mode and score follow the batch call; is_best and decision are
+ * not written (one alignment, no per-read decision).
+ * Memory: the working rows live in one fixed array inside the library,
+ * 3 * (65536 + 2) floats plus 256 bytes (about 0.8 MB) on every GPU that
+ * loads the library, held until the process exits.  n_events above 65536 is
+ * rejected with RA_EINVAL.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  Every call uses the same array and
+ * leaves its contents behind: calls whose work overlaps on the GPU (other
+ * streams, or other host threads) race and must be serialised by the caller.
+ * Returns RA_OK once the work is queued on cuda_stream (a cudaStream_t). */
+int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_events, const float *d_ref_signal,
+                               uint32_t m, int32_t band_w, int64_t slope_num, int64_t slope_den,
+                               int32_t end_mode, float b_match, rawalign_result_t *d_result,
+                               void *cuda_stream);
+
 /* Bytes of arena a batch of this shape needs (planning aid for callers). */
 uint64_t rawalign_dtw_batch_bytes(uint64_t n_events, uint32_t n_reads, uint32_t n_cands,
                                   uint64_t total_ref_values);

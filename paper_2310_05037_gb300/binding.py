@@ -116,6 +116,8 @@ SIGNATURES = {
     "rawalign_dtw_destroy": (C.c_int, [C.c_void_p]),
     "rawalign_dtw_batch_stats": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Stats)]),
     "rawalign_dtw_batch_bytes": (C.c_uint64, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64]),
+    "rawalign_dtw_align_noalloc": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_int32, C.c_int64,
+                                             C.c_int64, C.c_int32, C.c_float, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -227,6 +229,14 @@ def rawalign_dtw_batch_stats(h, batch: int) -> Stats:
 
 def rawalign_dtw_batch_bytes(n_events, n_reads, n_cands, total_ref_values) -> int:
     return int(load().rawalign_dtw_batch_bytes(int(n_events), int(n_reads), int(n_cands), int(total_ref_values)))
+
+
+def rawalign_dtw_align_noalloc(d_events: int, n_events: int, d_ref_signal: int, m: int, band_w: int, slope_num: int,
+                               slope_den: int, end_mode: int, b_match: float, d_result: int, stream: int) -> int:
+    """Device pointers in (ints); returns the status code (RA_OK when queued)."""
+    return int(load().rawalign_dtw_align_noalloc(C.c_void_p(d_events), n_events, C.c_void_p(d_ref_signal), m, band_w,
+                                                 slope_num, slope_den, end_mode, b_match, C.c_void_p(d_result),
+                                                 C.c_void_p(stream)))
 
 
 def rawalign_dtw_destroy(h) -> None:

@@ -582,4 +582,18 @@ extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
     return RA_OK;
 }
 
+// Band of one alignment for callers outside this file (same rule as the batch
+// planner): num/den/w as the kernels take them, and the w_eff to report.
+int ra::host_band(int64_t n, int64_t m, int32_t band_w, int64_t num, int64_t den, int64_t *num_out,
+                  int64_t *den_out, int64_t *w_out, int32_t *w_report)
+{
+    BandDef b;
+    if (band_for(n, m, band_w, num, den, b, *w_report) != 0)
+        return RA_EINVAL;
+    *num_out = b.num;
+    *den_out = b.den;
+    *w_out = b.w;
+    return RA_OK;
+}
+
 // Serving entry points are defined in serve.cu.

@@ -77,6 +77,8 @@ void set_mask_mode(int mode);  // 0: per-row compare, 1: per-step bit mask
 cudaError_t launch_plain(const WorkDesc *w, const float *events, const float *r_all, float *diag,
                          rawalign_result_t *results, unsigned long long *best_keys, float b_match,
                          int end_free, cudaStream_t s);
+int host_band(int64_t n, int64_t m, int32_t band_w, int64_t num, int64_t den, int64_t *num_out,
+              int64_t *den_out, int64_t *w_out, int32_t *w_report);
 cudaError_t launch_decide(rawalign_result_t *results, int n, const unsigned long long *best_keys,
                           const int *read_of, float thr, int final_decision, cudaStream_t s);
 
