@@ -333,6 +333,8 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
         return RA_EINVAL;
     if (config->end_mode != RA_END_GLOBAL && config->end_mode != RA_END_FREE)
         return RA_EINVAL;
+    if (config->serve_slots < 0 || config->serve_max_events < 0 || config->max_candidates < 0)
+        return RA_EINVAL;
     if (config->kernel < RA_KERNEL_AUTO || config->kernel == 2 || config->kernel == 3 ||
         config->kernel >= RA_KERNEL_VARIANT0 + kNumVariants)
         return RA_EINVAL;
@@ -462,10 +464,16 @@ extern "C" int rawalign_dtw_poll(rawalign_dtw_t *h, uint64_t ticket, rawalign_re
     if (!h || !n_out || (cap && !out))
         return RA_EINVAL;
     *n_out = 0;
+    cudaSetDevice(h->device);
+    {
+        bool handled = false;
+        int rc = serve_poll(h, ticket, out, cap, n_out, timeout_us, &handled);
+        if (handled)
+            return rc;
+    }
     auto it = h->tickets.find(ticket);
     if (it == h->tickets.end())
         return RA_EINVAL;
-    cudaSetDevice(h->device);
     Ticket &t = it->second;
     auto t0 = std::chrono::steady_clock::now();
     while (true) {
@@ -565,6 +573,7 @@ extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
         return RA_EINVAL;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
+    serve_destroy(h);
     for (auto &tk : h->tickets)
         if (tk.second.done)
             cudaEventDestroy(tk.second.done);

@@ -1,10 +1,604 @@
-// serve.cu -- Read-Until serving entry points (filled in below).
-#include "internal.cuh"
+// serve.cu -- Read-Until serving (Sec. 1, Sec. 3.1: decisions per chunk of
+// signal while the read is still in the pore).
+//
+// A read is admitted on its first chunk, with its candidate regions, if a read
+// slot is free and the arena can hold the read's device state: the expected
+// signal of every candidate (Sup. A.1.1) and two frontier rows per candidate.
+// The frontier is the band of the DTW row of the last event aligned so far;
+// the next chunk resumes the DP from it (Sec. 2.2), so a chunked read gives the
+// same DP as aligning its whole prefix at once.  Each chunk's cost is the
+// minimum over its last row (FREE end: the read prefix against a longer
+// reference window) and its score is B_Match * events so far - cost.
+//
+// submit_chunk only queues.  flush launches every queued chunk of every read
+// as one batch (continuous batching): chunks that arrive while a flush is on
+// the GPU go into the next flush, and the stream orders the flushes, so a
+// read's chunk k+1 always sees the frontier chunk k wrote.  A read's memory
+// and slot are returned when the flush carrying its last chunk completes.
+#include "engine.h"
 
-extern "C" int rawalign_dtw_submit_chunk(rawalign_dtw_t *, uint64_t, const float *, uint32_t,
-                                         const rawalign_candidate_t *, uint32_t, int, uint64_t *)
+namespace ra_host {
+
+struct ServeCand {
+    BandDef band;
+    int32_t w_report = 0;
+    uint64_t r_off = 0;     // floats from the arena base: expected signal (m values)
+    uint64_t fr_off[2] = {0, 0};  // floats from the arena base: frontier rows
+    uint32_t fr_cap = 0;    // floats per frontier row
+    int cur = 0;            // frontier holding the last processed row
+    int32_t fr_lo = -1, fr_wid = 0;  // its band (first column, width - 1)
+    uint32_t m = 0;
+    bool dead = false;      // the band has left the table: no cell any more
+    SigDesc sig{};
+};
+
+struct ServeRead {
+    uint64_t read_id = 0;
+    void *block = nullptr;  // arena block: expected signals + frontiers
+    uint32_t rows_done = 0;
+    std::vector<ServeCand> cands;
+    bool signal_done = false;
+    bool closed = false;
+};
+
+struct PendingChunk {
+    uint64_t read_id = 0;
+    std::vector<float> ev;
+    std::vector<uint64_t> tickets;
+    int last = 0;
+};
+
+// Pinned host staging buffers, reused across flushes (copies to and from
+// pageable memory would make the host wait for the device).
+struct PinnedPool {
+    std::multimap<size_t, void *> free_;
+    void *get(size_t bytes)
+    {
+        auto it = free_.lower_bound(bytes);
+        if (it != free_.end()) {
+            void *p = it->second;
+            free_.erase(it);
+            return p;
+        }
+        size_t cap = 1 << 16;
+        while (cap < bytes)
+            cap <<= 1;
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, cap, cudaHostAllocDefault) != cudaSuccess)
+            return nullptr;
+        sizes_[p] = cap;
+        return p;
+    }
+    void put(void *p)
+    {
+        if (p)
+            free_.emplace(sizes_[p], p);
+    }
+    ~PinnedPool()
+    {
+        for (auto &kv : sizes_)
+            cudaFreeHost(kv.first);
+    }
+    std::map<void *, size_t> sizes_;
+};
+
+struct FlushRec {
+    cudaEvent_t done = nullptr;
+    std::vector<void *> blocks;
+    rawalign_result_t *d_res = nullptr;
+    rawalign_result_t *h_res = nullptr;  // pinned
+    void *h_in = nullptr;                 // pinned inputs of this flush
+    struct T {
+        uint64_t ticket, read_id;
+        uint32_t first, count;
+        int last;
+    };
+    std::vector<T> tickets;
+    std::vector<uint64_t> closing;  // reads whose memory is returned on completion
+    bool reaped = false;
+};
+
+struct ServeState {
+    int slots = 0;
+    uint32_t max_events = 0;
+    int max_cands = 0;
+    int active = 0;
+    std::map<uint64_t, ServeRead> reads;
+    std::vector<PendingChunk> pending;
+    std::map<uint64_t, FlushRec *> flushes;       // by flush id
+    std::map<uint64_t, uint64_t> ticket_flush;    // ticket -> flush id
+    std::map<uint64_t, std::vector<rawalign_result_t>> ready;  // reaped results by ticket
+    uint64_t next_flush = 1;
+    PinnedPool pinned;
+};
+
+namespace {
+
+ServeState *state(rawalign_dtw *h)
 {
-    return RA_EINVAL;
+    if (!h->serve && h->cfg.serve_slots > 0) {
+        h->serve = new (std::nothrow) ServeState();
+        if (h->serve) {
+            h->serve->slots = h->cfg.serve_slots;
+            h->serve->max_events = h->cfg.serve_max_events > 0 ? (uint32_t)h->cfg.serve_max_events : 0;
+            h->serve->max_cands = h->cfg.max_candidates > 0 ? h->cfg.max_candidates : 64;
+        }
+    }
+    return h->serve;
 }
 
-extern "C" int rawalign_dtw_flush(rawalign_dtw_t *) { return RA_OK; }
+void release_read(rawalign_dtw *h, ServeState *st, uint64_t read_id)
+{
+    auto it = st->reads.find(read_id);
+    if (it == st->reads.end())
+        return;
+    h->arena.release(it->second.block);
+    st->reads.erase(it);
+    st->active--;
+}
+
+// Copies a completed flush's results to its tickets and returns its memory.
+void reap(rawalign_dtw *h, ServeState *st, uint64_t fid, FlushRec *f)
+{
+    if (f->reaped)
+        return;
+    for (auto &t : f->tickets) {
+        std::vector<rawalign_result_t> v(f->h_res + t.first, f->h_res + t.first + t.count);
+        for (uint32_t c = 0; c < t.count; ++c) {
+            v[c].read_id = t.read_id;
+            v[c].cand_idx = c;
+            if (t.last && v[c].decision == RA_PENDING)
+                v[c].decision = RA_UNMAPPED;
+        }
+        st->ready[t.ticket] = std::move(v);
+        st->ticket_flush.erase(t.ticket);
+    }
+    for (void *p : f->blocks)
+        h->arena.release(p);
+    f->blocks.clear();
+    st->pinned.put(f->h_res);
+    st->pinned.put(f->h_in);
+    for (uint64_t r : f->closing)
+        release_read(h, st, r);
+    cudaEventDestroy(f->done);
+    f->reaped = true;
+    st->flushes.erase(fid);
+    delete f;
+}
+
+void reap_done(rawalign_dtw *h, ServeState *st)
+{
+    std::vector<uint64_t> ids;
+    for (auto &kv : st->flushes)
+        if (cudaEventQuery(kv.second->done) == cudaSuccess)
+            ids.push_back(kv.first);
+    for (uint64_t id : ids)
+        reap(h, st, id, st->flushes[id]);
+}
+
+}  // namespace
+
+void serve_destroy(rawalign_dtw *h)
+{
+    ServeState *st = h->serve;
+    if (!st)
+        return;
+    cudaStreamSynchronize(h->stream);
+    std::vector<uint64_t> ids;
+    for (auto &kv : st->flushes)
+        ids.push_back(kv.first);
+    for (uint64_t id : ids)
+        reap(h, st, id, st->flushes[id]);
+    std::vector<uint64_t> rs;
+    for (auto &kv : st->reads)
+        rs.push_back(kv.first);
+    for (uint64_t r : rs)
+        release_read(h, st, r);
+    delete st;
+    h->serve = nullptr;
+}
+
+int serve_poll(rawalign_dtw *h, uint64_t ticket, rawalign_result_t *out, uint32_t cap, uint32_t *n_out,
+               int64_t timeout_us, bool *handled)
+{
+    *handled = false;
+    ServeState *st = h->serve;
+    if (!st)
+        return RA_OK;
+    auto r = st->ready.find(ticket);
+    if (r == st->ready.end()) {
+        auto tf = st->ticket_flush.find(ticket);
+        if (tf == st->ticket_flush.end()) {
+            // queued but not flushed yet?
+            for (auto &pc : st->pending)
+                for (uint64_t t : pc.tickets)
+                    if (t == ticket) {
+                        *handled = true;
+                        return RA_ENOTREADY;
+                    }
+            return RA_OK;  // not a serving ticket
+        }
+        *handled = true;
+        FlushRec *f = st->flushes[tf->second];
+        auto t0 = std::chrono::steady_clock::now();
+        while (true) {
+            cudaError_t e = cudaEventQuery(f->done);
+            if (e == cudaSuccess)
+                break;
+            if (e != cudaErrorNotReady)
+                return cuda_ok(e);
+            if (timeout_us == 0)
+                return RA_ENOTREADY;
+            if (timeout_us > 0) {
+                auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0);
+                if (el.count() >= timeout_us)
+                    return RA_ENOTREADY;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(10));
+        }
+        reap(h, st, tf->second, f);
+        r = st->ready.find(ticket);
+        if (r == st->ready.end())
+            return RA_EDEVICE;
+    }
+    *handled = true;
+    uint32_t n = std::min<uint32_t>(cap, (uint32_t)r->second.size());
+    if (n)
+        memcpy(out, r->second.data(), sizeof(rawalign_result_t) * n);
+    *n_out = n;
+    st->ready.erase(r);
+    return RA_OK;
+}
+
+}  // namespace ra_host
+
+extern "C" int rawalign_dtw_submit_chunk(rawalign_dtw_t *h, uint64_t read_id, const float *events, uint32_t n_events,
+                                         const rawalign_candidate_t *cands, uint32_t n_cands, int last,
+                                         uint64_t *ticket)
+{
+    if (!h || !ticket || (n_events && !events))
+        return RA_EINVAL;
+    ServeState *st = state(h);
+    if (!st)
+        return RA_EINVAL;  // serving not configured (serve_slots == 0)
+    cudaSetDevice(h->device);
+    for (uint32_t x = 0; x < n_events; ++x)
+        if (!std::isfinite(events[x]))
+            return RA_EINVAL;
+    auto it = st->reads.find(read_id);
+    if (it == st->reads.end()) {
+        // admission: a read slot and arena memory for the read's device state
+        if (!cands || n_cands == 0 || (int)n_cands > st->max_cands)
+            return RA_EINVAL;
+        const int k = h->cfg.k;
+        ServeRead rd;
+        rd.read_id = read_id;
+        uint64_t floats = 0;
+        for (uint32_t c = 0; c < n_cands; ++c) {
+            const rawalign_candidate_t &cd = cands[c];
+            if (cd.strand > 1 || cd.slope_den <= 0 || cd.slope_num < 0)
+                return RA_EINVAL;
+            if (cd.ref_offset > h->ref_len || cd.ref_len_bases > h->ref_len - cd.ref_offset ||
+                (int64_t)cd.ref_len_bases < k || cd.ref_len_bases >= (1u << 30))
+                return RA_EINVAL;
+            ServeCand sc;
+            sc.m = cd.ref_len_bases - k + 1;
+            // rows are unknown until the read ends: the slope must be given;
+            // n = 2 keeps the band rule from treating the piece as one row
+            if (band_for(2, sc.m, cd.band_w, cd.slope_num, cd.slope_den, sc.band, sc.w_report) != 0)
+                return RA_EINVAL;
+            sc.fr_cap = (uint32_t)std::min<int64_t>(2 * sc.band.w + 2, (int64_t)sc.m + 1);
+            sc.sig.ref_off = cd.ref_offset;
+            sc.sig.len = cd.ref_len_bases;
+            sc.sig.strand = cd.strand;
+            floats += ((sc.m + 63) & ~63u) + 2ull * ((sc.fr_cap + 63) & ~63u);
+            rd.cands.push_back(sc);
+        }
+        if (st->active >= st->slots)
+            return RA_EAGAIN;
+        rd.block = h->arena.alloc(floats * sizeof(float));
+        if (!rd.block) {
+            reap_done(h, st);
+            rd.block = h->arena.alloc(floats * sizeof(float));
+            if (!rd.block)
+                return RA_EAGAIN;  // admission refused by free HBM in the arena
+        }
+        uint64_t off = (uint64_t)((char *)rd.block - h->arena.base) / sizeof(float);
+        for (auto &sc : rd.cands) {
+            sc.r_off = off;
+            sc.sig.r_off = off;
+            off += (sc.m + 63) & ~63u;
+            sc.fr_off[0] = off;
+            off += (sc.fr_cap + 63) & ~63u;
+            sc.fr_off[1] = off;
+            off += (sc.fr_cap + 63) & ~63u;
+        }
+        st->active++;
+        it = st->reads.emplace(read_id, std::move(rd)).first;
+    } else if (cands) {
+        return RA_EINVAL;  // candidates come with the first chunk only
+    }
+    ServeRead &rd = it->second;
+    if (rd.closed)
+        return RA_EINVAL;
+    // one pending chunk per read per flush: later chunks join it
+    PendingChunk *pc = nullptr;
+    for (auto &p : st->pending)
+        if (p.read_id == read_id)
+            pc = &p;
+    uint64_t queued = pc ? pc->ev.size() : 0;
+    if (st->max_events && rd.rows_done + queued + n_events > st->max_events)
+        return RA_EINVAL;
+    if (!pc) {
+        st->pending.push_back(PendingChunk());
+        pc = &st->pending.back();
+        pc->read_id = read_id;
+    }
+    pc->ev.insert(pc->ev.end(), events, events + n_events);
+    pc->last = pc->last || last;
+    if (last)
+        rd.closed = true;
+    uint64_t t = h->next_id++;
+    pc->tickets.push_back(t);
+    *ticket = t;
+    return RA_OK;
+}
+
+extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
+{
+    if (!h)
+        return RA_EINVAL;
+    ServeState *st = h->serve;
+    if (!st)
+        return RA_OK;
+    cudaSetDevice(h->device);
+    reap_done(h, st);
+    if (st->pending.empty())
+        return RA_OK;
+    // plan: one piece of work per (chunk, candidate)
+    std::vector<float> ev;
+    std::vector<SigDesc> sig;
+    struct Item {
+        WorkDesc wd;
+        int variant;
+        double cost;
+    };
+    std::vector<Item> items;
+    std::vector<int> read_of;
+    FlushRec *f = new FlushRec();
+    struct Update {  // host state advanced only once the flush is launched
+        ServeCand *sc;
+        int32_t fr_lo, fr_wid;
+        bool dead;
+    };
+    std::vector<Update> updates;
+    uint32_t chunk_idx = 0;
+    for (auto &pc : st->pending) {
+        ServeRead &rd = st->reads[pc.read_id];
+        const uint32_t row0 = rd.rows_done, nrows = (uint32_t)pc.ev.size();
+        const uint64_t ev_off = ev.size();
+        ev.insert(ev.end(), pc.ev.begin(), pc.ev.end());
+        const uint32_t first = (uint32_t)items.size();
+        const uint32_t count = nrows ? (uint32_t)rd.cands.size() : 0;  // a close-only chunk returns nothing
+        for (uint32_t c = 0; c < count; ++c) {
+            ServeCand &sc = rd.cands[c];
+            if (!rd.signal_done)
+                sig.push_back(sc.sig);
+            Item it;
+            memset(&it.wd, 0, sizeof(WorkDesc));
+            WorkDesc &wd = it.wd;
+            wd.ev_off = ev_off;
+            wd.r_off = sc.r_off;
+            wd.num = sc.band.num;
+            wd.den = sc.band.den;
+            wd.row0 = (int32_t)row0;
+            wd.nrows = (int32_t)nrows;
+            wd.m = (int32_t)sc.m;
+            wd.w = (int32_t)sc.band.w;
+            wd.cand = (int32_t)items.size();
+            wd.read = (int32_t)chunk_idx;
+            wd.n_read = (int32_t)(row0 + nrows);
+            wd.w_report = sc.w_report;
+            if (row0 == 0) {
+                wd.fin_off = ~0ull;
+                wd.fin_lo = -1;
+                wd.fin_wid = 0;
+            } else {
+                wd.fin_off = sc.fr_off[sc.cur];
+                wd.fin_lo = sc.fr_lo;
+                wd.fin_wid = sc.fr_wid;
+            }
+            wd.fout_off = sc.fr_off[1 - sc.cur];
+            const int64_t last_row = (int64_t)row0 + nrows - 1;
+            wd.fout_lo = (int32_t)sc.band.lo(last_row);
+            Sched sch;
+            if (sc.dead) {
+                it.variant = 0;
+                sch.s_end = 0;
+            } else {
+                it.variant = choose_variant(sc.band, row0, nrows, sch);
+            }
+            wd.dC = sch.dC;
+            wd.a0 = sch.a0;
+            wd.s_end = sch.s_end;
+            it.cost = (double)sch.s_end * kVariants[it.variant][0];
+            items.push_back(it);
+            read_of.push_back((int)chunk_idx);
+            // the band of this piece's last row is the row above the next piece
+            Update u{&sc, sc.fr_lo, sc.fr_wid, sc.dead};
+            if (!sc.dead) {
+                const int64_t lo = sc.band.lo(last_row), hi = sc.band.hi(last_row);
+                if (hi >= lo && sch.s_end > 0) {
+                    u.fr_lo = (int32_t)lo;
+                    u.fr_wid = (int32_t)(hi - lo);
+                } else {
+                    u.dead = true;
+                }
+            }
+            updates.push_back(u);
+        }
+        for (uint64_t t : pc.tickets)
+            f->tickets.push_back({t, pc.read_id, first, count, pc.last});
+        if (pc.last)
+            f->closing.push_back(pc.read_id);
+        chunk_idx++;
+    }
+    const uint32_t n_items = (uint32_t)items.size();
+    if (n_items == 0) {
+        // only close-only chunks: nothing to run
+        f->h_res = nullptr;
+        RA_CUDA(cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming));
+        RA_CUDA(cudaEventRecord(f->done, h->stream));
+        const uint64_t fid = st->next_flush++;
+        st->flushes[fid] = f;
+        for (auto &t : f->tickets)
+            st->ticket_flush[t.ticket] = fid;
+        st->pending.clear();
+        return RA_OK;
+    }
+    std::vector<int> order(n_items);
+    for (uint32_t x = 0; x < n_items; ++x)
+        order[x] = (int)x;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (items[x].variant != items[y].variant)
+            return items[x].variant < items[y].variant;
+        return items[x].cost > items[y].cost;
+    });
+    std::vector<WorkDesc> work(n_items);
+    for (uint32_t x = 0; x < n_items; ++x)
+        work[x] = items[order[x]].wd;
+    // device memory for this flush
+    auto take = [&](uint64_t bytes) -> void * {
+        void *p = h->arena.alloc(std::max<uint64_t>(bytes, 256));
+        if (p)
+            f->blocks.push_back(p);
+        return p;
+    };
+    float *d_ev = (float *)take(sizeof(float) * ev.size());
+    SigDesc *d_sig = (SigDesc *)take(sizeof(SigDesc) * sig.size());
+    WorkDesc *d_work = (WorkDesc *)take(sizeof(WorkDesc) * n_items);
+    f->d_res = (rawalign_result_t *)take(sizeof(rawalign_result_t) * n_items);
+    unsigned long long *d_keys = (unsigned long long *)take(sizeof(unsigned long long) * chunk_idx);
+    int *d_read_of = (int *)take(sizeof(int) * n_items);
+    int *d_queue = (int *)take(sizeof(int) * (kNumVariants + 2));
+    bool ok = d_ev && d_sig && d_work && f->d_res && d_keys && d_read_of && d_queue;
+    std::vector<ClassLaunch> classes;
+    if (ok) {
+        int pos = 0;
+        for (int v = 0; v < kNumVariants && ok; ++v) {
+            ClassLaunch cl;
+            cl.G = kVariants[v][0];
+            cl.HR = kVariants[v][1];
+            cl.first = pos;
+            int64_t need = 4;
+            while (pos < (int)n_items && items[order[pos]].variant == v) {
+                need = std::max<int64_t>(need, (int64_t)work[pos].dC + 2);
+                need = std::max<int64_t>(need, (int64_t)work[pos].fin_wid + cl.G + 2);
+                ++pos;
+            }
+            cl.count = pos - cl.first;
+            if (cl.count == 0)
+                continue;
+            cl.max_cost = items[order[cl.first]].cost;
+            cl.ring_cap = next_pow2(need);
+            const int gpb = kBlock / cl.G;
+            size_t smem = (size_t)gpb * (cl.ring_cap + 1) * sizeof(float);
+            cl.ring_in_smem = smem <= 64 * 1024;
+            cl.smem = cl.ring_in_smem ? smem : 0;
+            int nb = stripe_max_blocks_per_sm(cl.G, cl.HR, kBlock, cl.smem);
+            if (nb <= 0) {
+                ok = false;
+                break;
+            }
+            cl.grid = std::max(1, std::min(h->sm_count * nb, (cl.count + gpb - 1) / gpb));
+            if (!cl.ring_in_smem) {
+                cl.gring = (float *)take(sizeof(float) * (uint64_t)cl.grid * gpb * cl.ring_cap);
+                ok = cl.gring != nullptr;
+            }
+            classes.push_back(cl);
+        }
+    }
+    // pinned staging: inputs in one buffer, results in another
+    const size_t b_ev = sizeof(float) * ev.size(), b_sig = sizeof(SigDesc) * sig.size();
+    const size_t b_work = sizeof(WorkDesc) * n_items, b_rd = sizeof(int) * n_items;
+    const size_t o_sig = (b_ev + 255) & ~255ull, o_work = o_sig + ((b_sig + 255) & ~255ull);
+    const size_t o_rd = o_work + ((b_work + 255) & ~255ull), in_bytes = o_rd + b_rd + 256;
+    if (ok) {
+        f->h_in = st->pinned.get(in_bytes);
+        f->h_res = (rawalign_result_t *)st->pinned.get(sizeof(rawalign_result_t) * std::max<uint32_t>(n_items, 1));
+        ok = f->h_in && f->h_res;
+    }
+    if (!ok) {
+        // nothing was launched and no host state advanced
+        for (void *p : f->blocks)
+            h->arena.release(p);
+        st->pinned.put(f->h_in);
+        st->pinned.put(f->h_res);
+        delete f;
+        return RA_ENOMEM;
+    }
+    char *hin = (char *)f->h_in;
+    memcpy(hin, ev.data(), b_ev);
+    memcpy(hin + o_sig, sig.data(), b_sig);
+    memcpy(hin + o_work, work.data(), b_work);
+    memcpy(hin + o_rd, read_of.data(), b_rd);
+    cudaStream_t s = h->stream;
+    RA_CUDA(cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming));
+    RA_CUDA(cudaMemcpyAsync(d_ev, hin, b_ev, cudaMemcpyHostToDevice, s));
+    if (!sig.empty())
+        RA_CUDA(cudaMemcpyAsync(d_sig, hin + o_sig, b_sig, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(d_work, hin + o_work, b_work, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(d_read_of, hin + o_rd, b_rd, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemsetAsync(d_keys, 0, sizeof(unsigned long long) * chunk_idx, s));
+    RA_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int) * (kNumVariants + 2), s));
+    float *abase = (float *)h->arena.base;
+    if (!sig.empty())
+        RA_CUDA(launch_expected_signal(d_sig, (int)sig.size(), h->d_ref, h->d_pore, h->cfg.k, abase, s));
+    RA_CUDA(cudaEventRecord(h->fork, s));
+    for (size_t ci = 0; ci < classes.size(); ++ci) {
+        auto &cl = classes[ci];
+        cudaStream_t cs = h->aux[ci];
+        RA_CUDA(cudaStreamWaitEvent(cs, h->fork, 0));
+        StripeParams p{};
+        p.work = d_work + cl.first;
+        p.n_work = cl.count;
+        p.queue = d_queue + ci;
+        p.events = d_ev;
+        p.r_all = abase;
+        p.fstore = abase;
+        p.fstore_out = abase;
+        p.results = f->d_res;
+        p.best_keys = d_keys;
+        p.gring = cl.gring;
+        p.ring_cap = cl.ring_cap;
+        p.ring_in_smem = cl.ring_in_smem;
+        p.b_match = h->cfg.b_match;
+        p.end_free = 1;
+        p.err = d_queue + kNumVariants;
+        RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
+        RA_CUDA(cudaEventRecord(h->join[ci], cs));
+        RA_CUDA(cudaStreamWaitEvent(s, h->join[ci], 0));
+    }
+    RA_CUDA(launch_decide(f->d_res, (int)n_items, d_keys, d_read_of, h->cfg.score_threshold, 0, s));
+    RA_CUDA(cudaMemcpyAsync(f->h_res, f->d_res, sizeof(rawalign_result_t) * n_items, cudaMemcpyDeviceToHost, s));
+    RA_CUDA(cudaEventRecord(f->done, s));
+    // launched: advance the host-side read state
+    for (auto &u : updates) {
+        if (!u.sc->dead)
+            u.sc->cur = 1 - u.sc->cur;
+        u.sc->fr_lo = u.fr_lo;
+        u.sc->fr_wid = u.fr_wid;
+        u.sc->dead = u.dead;
+    }
+    for (auto &pc : st->pending) {
+        ServeRead &rd = st->reads[pc.read_id];
+        rd.signal_done = true;
+        rd.rows_done += (uint32_t)pc.ev.size();
+    }
+    const uint64_t fid = st->next_flush++;
+    st->flushes[fid] = f;
+    for (auto &t : f->tickets)
+        st->ticket_flush[t.ticket] = fid;
+    st->pending.clear();
+    return RA_OK;
+}

@@ -105,14 +105,11 @@ def write_bases(ref2bit: np.ndarray, start: int, codes: np.ndarray) -> None:
 def write_bases_fast(ref2bit: np.ndarray, start: int, codes: np.ndarray) -> None:
     n = len(codes)
     pos = start + np.arange(n, dtype=np.int64)
-    full = np.zeros(0)
-    # unpack touched bytes, modify, repack
+    # unpack the touched bytes, modify, repack
     b0, b1 = start // 4, (start + n + 3) // 4
-    cur = unpack_bases(ref2bit, 4 * b0, 4 * (b1 - b0))
-    cur = cur.copy()
+    cur = unpack_bases(ref2bit, 4 * b0, 4 * (b1 - b0)).copy()
     cur[pos - 4 * b0] = codes
     ref2bit[b0:b1] = pack_bases(cur)
-    del full
 
 
 def pore_table(seed: int) -> np.ndarray:
@@ -362,15 +359,17 @@ def config_serving(seed: int = 0x5EED0004, n_reads: int = 2048, ref_len: int = 1
                    rate_per_s: float = 1280.0):
     """Serving loop inputs: reads that arrive as a Poisson stream (mean rate
     chosen so that about 512 are in flight at 0.4 s per 180-event chunk),
-    <= 4000 events each, up to 32 candidates (1 true when on-target), band 64,
-    slope 1.1 reference values per event given per candidate.  Returns
+    <= 4000 events each, up to 32 candidates (1 true when on-target), band 64.
+    Each candidate carries the band slope the sequencer model implies:
+    1 / (0.95 * 1.1) = 1000/1045 reference values per event (mean dwell 1.1
+    events per k-mer, 5 % skipped k-mers).  Returns
     (pore, ref2bit, ref_len, [ServingRead])."""
     rng = np.random.Generator(np.random.PCG64(seed))
     pore = pore_table(seed ^ 0xA5A5)
     ref = hashed_reference(seed, ref_len)
     out = []
     t = 0.0
-    span = int(math.ceil(max_events * 1.1)) + 2 * band + K
+    span = int(math.ceil(max_events * 1000 / 1045)) + 2 * band + K
     for q in range(n_reads):
         t += rng.exponential(1.0 / rate_per_s)
         loc = int(rng.integers(0, ref_len - 3 * max_events - span))
@@ -386,7 +385,7 @@ def config_serving(seed: int = 0x5EED0004, n_reads: int = 2048, ref_len: int = 1
         true_slot = int(rng.integers(0, nc))
         for s in range(nc):
             off = loc if (on and s == true_slot) else int(rng.integers(0, ref_len - span))
-            c[s] = (q, off, span, 0, 0, band, 0, 11, 10)
+            c[s] = (q, off, span, 0, 0, band, 0, 1000, 1045)
         out.append(ServingRead(q, ev, c, on, t))
     return pore, ref, ref_len, out
 
