@@ -179,6 +179,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-chunks", type=int, default=10000)
+    ap.add_argument("--serve-realtime-s", type=float, default=6.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -312,6 +315,26 @@ def main():
                       "h2d_bytes_per_step": int(w.events.nbytes + w.read_offsets.nbytes + w.cands.nbytes),
                       "d2h_bytes_per_step": int(w.n_cands * B.RESULT_DTYPE.itemsize),
                       "ms_per_step": round(el / e2e_steps * 1e3, 2)}
+
+    # Read-Until serving: 512 reads in flight, 180-event chunks, <= 4000 events
+    if not args.no_serve and rank == 0:
+        from paper_2310_05037_gb300.serving import ServingLoop
+
+        pore_s, ref_s, rl_s, sreads = S.config_serving(n_reads=4096)
+        als = B.Aligner(pore_s, ref_s, rl_s, arena_bytes=(len(ref_s) + (1536 << 20)), serve_slots=512,
+                        serve_max_events=4000, max_candidates=32, device="cuda:%d" % local)
+        loop = ServingLoop(als, sreads[:64])
+        loop.run(max_chunks=300, in_flight=64)  # warm-up
+        loop = ServingLoop(als, sreads)
+        closed = loop.run(max_chunks=args.serve_chunks, in_flight=512).summary()
+        rt = ServingLoop(als, sreads[::-1]).run(max_chunks=10 ** 9, in_flight=512, realtime=True, chunk_s=0.4,
+                                                 duration_s=args.serve_realtime_s, arrival_rate=1280.0).summary()
+        als.close()
+        out["served"] = {"closed_loop": closed, "realtime": rt,
+                         "workload": "Read-Until serving: Poisson stream, 512 reads in flight, 180-event chunks, "
+                                     "<= 4000 events, 1-32 candidates, band 64, FREE end, 50% off-target reads"}
+        out["speedup_served_vs_plain"] = (round(closed["gcups"] / out["plain_kernel"]["gcups"], 1)
+                                          if "plain_kernel" in out else None)
 
     if not args.no_cpu and rank == 0 and world >= 1:
         cb = cpu_baseline(w, seconds=args.cpu_seconds)

@@ -180,3 +180,23 @@ def test_decision_maps_true_locus():
         assert set(hist[-1][1]["decision"]) <= {B.RA_MAPPED, B.RA_UNMAPPED}
         if rd.on_target:
             assert hist[-1][1]["decision"][0] == B.RA_MAPPED
+
+
+def test_request_loop_closed_and_realtime():
+    """The request loop decides every read it admits and keeps latencies."""
+    from paper_2310_05037_gb300.serving import ServingLoop
+
+    pore, ref, ref_len, reads = _serving_inputs(n_reads=40, max_events=1200, seed=11)
+    al = _aligner(pore, ref, ref_len, slots=16, max_events=1200)
+    try:
+        st = ServingLoop(al, reads, max_events=1200).run(max_chunks=10 ** 6, in_flight=16)
+        assert st.reads_done == len(reads)
+        assert st.accepted + st.rejected + st.exhausted == st.reads_done
+        assert st.chunks == len(st.latencies_ms) and st.cells > 0
+        on = sum(rd.on_target for rd in reads)
+        assert st.accepted >= on * 0.8
+        rt = ServingLoop(al, reads[:8], max_events=1200).run(max_chunks=10 ** 6, in_flight=8, realtime=True,
+                                                            chunk_s=0.05, duration_s=5.0, arrival_rate=100.0)
+        assert rt.chunks > 0
+    finally:
+        al.close()
