@@ -49,12 +49,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         return RA_EINVAL;
     if (b.n_events >= (1ull << 40))
         return RA_EINVAL;
-    struct Item {
-        WorkDesc wd;
-        int variant;
-        double cost;
-    };
-    std::vector<Item> items(n_cands);
+    std::vector<PlanItem> items(n_cands);
     std::vector<SigDesc> sig(n_cands);
     uint64_t r_total = 0;
     b.cells = 0;
@@ -75,7 +70,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         int32_t wrep;
         if (band_for(n, m, cd.band_w, cd.slope_num, cd.slope_den, band, wrep) != 0)
             return RA_EINVAL;
-        Item &it = items[c];
+        PlanItem &it = items[c];
         memset(&it.wd, 0, sizeof(WorkDesc));
         WorkDesc &wd = it.wd;
         wd.ev_off = offs[cd.read_id];
@@ -105,6 +100,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         wd.a0 = s.a0;
         wd.s_end = s.s_end;
         it.cost = (double)s.s_end * kVariants[it.variant][0];
+        it.cap = ring_need(wd, kVariants[it.variant][0]);
         b.max_rows = std::max<int>(b.max_rows, (int)n);
         sig[c].ref_off = cd.ref_offset;
         sig[c].r_off = r_total;
@@ -112,15 +108,13 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         sig[c].strand = cd.strand;
         r_total += (uint64_t)m;
     }
-    // order: by variant, longest first
-    std::vector<int> order(n_cands);
-    for (uint32_t c = 0; c < n_cands; ++c)
-        order[c] = (int)c;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (items[x].variant != items[y].variant)
-            return items[x].variant < items[y].variant;
-        return items[x].cost > items[y].cost;
-    });
+    // launch order and classes (variant x ring size), longest first
+    std::vector<int> order;
+    b.classes.clear();
+    if (!make_classes(items, order, b.classes))
+        return RA_EINVAL;
+    if (b.plain)
+        b.classes.clear();
     std::vector<WorkDesc> work(n_cands);
     std::vector<int> read_of(n_cands);
     for (uint32_t c = 0; c < n_cands; ++c) {
@@ -135,57 +129,20 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     b.d_results = take<rawalign_result_t>(h, b, n_cands);
     b.d_keys = take<unsigned long long>(h, b, n_reads);
     b.d_read_of = take<int>(h, b, n_cands);
-    b.d_queue = take<int>(h, b, kNumVariants + 2);
+    b.d_queue = take<int>(h, b, kMaxClasses + 2);
     if (!b.d_events || !b.d_sig || !b.d_r || !b.d_work || !b.d_results || !b.d_keys || !b.d_read_of ||
         !b.d_queue)
         return RA_ENOMEM;
-    b.d_err = b.d_queue + kNumVariants;
+    b.d_err = b.d_queue + kMaxClasses;
     if (b.plain) {
         b.d_plain_diag = take<float>(h, b, 3ull * (b.max_rows + 2));
         if (!b.d_plain_diag)
             return RA_ENOMEM;
     }
-    // classes and ring buffers
-    b.classes.clear();
-    if (!b.plain) {
-        int pos = 0;
-        for (int v = 0; v < kNumVariants; ++v) {
-            ClassLaunch cl;
-            cl.G = kVariants[v][0];
-            cl.HR = kVariants[v][1];
-            cl.first = pos;
-            int64_t need = 4;
-            while (pos < (int)n_cands && items[order[pos]].variant == v) {
-                need = std::max<int64_t>(need, (int64_t)work[pos].dC + 2);
-                need = std::max<int64_t>(need, (int64_t)work[pos].fin_wid + 2);
-                ++pos;
-            }
-            cl.count = pos - cl.first;
-            if (cl.count == 0)
-                continue;
-            cl.max_cost = items[order[cl.first]].cost;
-            cl.ring_cap = next_pow2(need);
-            const int groups_per_block = kBlock / cl.G;
-            size_t smem = (size_t)groups_per_block * (cl.ring_cap + 1) * sizeof(float);
-            cl.ring_in_smem = smem <= 64 * 1024;
-            cl.smem = cl.ring_in_smem ? smem : 0;
-            int nb = stripe_max_blocks_per_sm(cl.G, cl.HR, kBlock, cl.smem);
-            if (nb <= 0)
-                return RA_EDEVICE;
-            int grid = h->sm_count * nb;
-            const int needed_blocks = (cl.count + groups_per_block - 1) / groups_per_block;
-            cl.grid = std::max(1, std::min(grid, needed_blocks));
-            if (!cl.ring_in_smem) {
-                cl.gring = take<float>(h, b, (uint64_t)cl.grid * groups_per_block * cl.ring_cap);
-                if (!cl.gring)
-                    return RA_ENOMEM;
-            }
-            b.classes.push_back(cl);
-        }
-        // the class holding the longest alignments starts first
-        std::stable_sort(b.classes.begin(), b.classes.end(),
-                         [](const ClassLaunch &x, const ClassLaunch &y) { return x.max_cost > y.max_cost; });
-    }
+    // launch geometry and global rings where shared memory is too small
+    int rc = finalize_classes(h->sm_count, b.classes, [&](uint64_t bytes) { return (void *)take<char>(h, b, bytes); });
+    if (rc != RA_OK)
+        return rc;
     cudaStream_t s = h->stream;
     RA_CUDA(cudaMemcpyAsync(b.d_events, events, sizeof(float) * b.n_events, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_sig, sig.data(), sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
@@ -206,7 +163,7 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
     cudaStream_t s = h->stream;
     if (part == 0) {
         RA_CUDA(cudaMemsetAsync(b.d_keys, 0, sizeof(unsigned long long) * std::max<uint32_t>(b.n_reads, 1), s));
-        RA_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int) * (kNumVariants + 2), s));
+        RA_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int) * (kMaxClasses + 2), s));
         RA_CUDA(launch_check_events(b.d_events, b.n_events, b.d_err, s));
         launches += b.n_events ? 1 : 0;
         RA_CUDA(launch_expected_signal(b.d_sig, (int)b.n_cands, h->d_ref, h->d_pore, h->cfg.k, b.d_r, s));
@@ -352,7 +309,7 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
     h->stream = (cudaStream_t)config->cuda_stream;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
-    for (int v = 0; v < kNumVariants; ++v) {
+    for (int v = 0; v < kMaxClasses; ++v) {
         if (cudaStreamCreateWithFlags(&h->aux[v], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&h->join[v], cudaEventDisableTiming) != cudaSuccess) {
             delete h;
@@ -579,7 +536,7 @@ extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
             cudaEventDestroy(tk.second.done);
     for (auto &b : h->batches)
         free_batch(h, b.second);
-    for (int v = 0; v < kNumVariants; ++v) {
+    for (int v = 0; v < kMaxClasses; ++v) {
         if (h->aux[v])
             cudaStreamDestroy(h->aux[v]);
         if (h->join[v])

@@ -27,6 +27,8 @@ constexpr int kBlock = 128;
 const int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}};
 const double kSlotCost[] = {1.0, 1.0, 1.25, 1.25, 1.25, 1.25};
 constexpr int kNumVariants = 6;
+constexpr int kMaxClasses = 64;              // launches per run (variant x ring size)
+constexpr size_t kSmemRingLimit = 96 * 1024; // larger rings go to global memory
 
 // ---------------------------------------------------------------- band math
 inline int64_t fdiv(int64_t a, int64_t b)
@@ -224,8 +226,8 @@ using namespace ra_host;
 struct rawalign_dtw {
     rawalign_dtw_config_t cfg{};
     cudaStream_t stream = nullptr;
-    cudaStream_t aux[kNumVariants] = {};   // one branch per kernel variant
-    cudaEvent_t fork = nullptr, join[kNumVariants] = {};
+    cudaStream_t aux[kMaxClasses] = {};   // one graph branch per launch class
+    cudaEvent_t fork = nullptr, join[kMaxClasses] = {};
     int device = 0;
     int sm_count = 152;
     Arena arena;
@@ -286,6 +288,89 @@ inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &o
         }
     }
     return best;
+}
+
+// One piece of work as planned on the host.
+struct PlanItem {
+    WorkDesc wd;
+    int variant = 0;
+    int cap = 0;        // ring entries the piece needs (power of two)
+    double cost = 0;    // lane-steps: longest first
+};
+
+// Sorts the items into launch order (variant, ring size, longest first) and
+// cuts them into launch classes of one variant and one ring size, so that a
+// few alignments with very wide bands do not force a large ring (and fewer
+// resident blocks, or a ring in global memory) on everything else.  Classes
+// are returned longest-alignment first.  Returns false if more than
+// kMaxClasses would be needed.
+inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &order, std::vector<ClassLaunch> &classes)
+{
+    const size_t n = items.size();
+    order.resize(n);
+    for (size_t x = 0; x < n; ++x)
+        order[x] = (int)x;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (items[x].variant != items[y].variant)
+            return items[x].variant < items[y].variant;
+        if (items[x].cap != items[y].cap)
+            return items[x].cap < items[y].cap;
+        return items[x].cost > items[y].cost;
+    });
+    classes.clear();
+    size_t pos = 0;
+    while (pos < n) {
+        const PlanItem &f = items[order[pos]];
+        ClassLaunch cl;
+        cl.G = kVariants[f.variant][0];
+        cl.HR = kVariants[f.variant][1];
+        cl.first = (int)pos;
+        cl.ring_cap = f.cap;
+        cl.max_cost = f.cost;
+        while (pos < n && items[order[pos]].variant == f.variant && items[order[pos]].cap == f.cap) {
+            cl.max_cost = std::max(cl.max_cost, items[order[pos]].cost);
+            ++pos;
+        }
+        cl.count = (int)pos - cl.first;
+        classes.push_back(cl);
+    }
+    if (classes.size() > (size_t)kMaxClasses)
+        return false;
+    std::stable_sort(classes.begin(), classes.end(),
+                     [](const ClassLaunch &x, const ClassLaunch &y) { return x.max_cost > y.max_cost; });
+    return true;
+}
+
+// Ring entries one piece needs: the stripe period plus two (written one step
+// before read) and room for the stored row above (serving).
+inline int ring_need(const WorkDesc &wd, int G)
+{
+    int64_t need = std::max<int64_t>((int64_t)wd.dC + 2, (int64_t)wd.fin_wid + G + 2);
+    return next_pow2(std::max<int64_t>(need, 128));
+}
+
+// Launch geometry of each class: ring in shared memory when it fits, grid of
+// as many resident blocks as the SMs hold (capped by the work), and a global
+// ring (from alloc(bytes)) otherwise.  Returns RA_OK, RA_ENOMEM or RA_EDEVICE.
+template <typename Alloc>
+int finalize_classes(int sm_count, std::vector<ClassLaunch> &classes, Alloc alloc)
+{
+    for (auto &cl : classes) {
+        const int gpb = kBlock / cl.G;
+        const size_t smem = (size_t)gpb * (cl.ring_cap + 1) * sizeof(float);
+        cl.ring_in_smem = smem <= kSmemRingLimit;
+        cl.smem = cl.ring_in_smem ? smem : 0;
+        const int nb = stripe_max_blocks_per_sm(cl.G, cl.HR, kBlock, cl.smem);
+        if (nb <= 0)
+            return RA_EDEVICE;
+        cl.grid = std::max(1, std::min(sm_count * nb, (cl.count + gpb - 1) / gpb));
+        if (!cl.ring_in_smem) {
+            cl.gring = (float *)alloc(sizeof(float) * (uint64_t)cl.grid * gpb * cl.ring_cap);
+            if (!cl.gring)
+                return RA_ENOMEM;
+        }
+    }
+    return RA_OK;
 }
 
 // serving entry points' helpers (serve.cu)

@@ -358,12 +358,7 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
     // plan: one piece of work per (chunk, candidate)
     std::vector<float> ev;
     std::vector<SigDesc> sig;
-    struct Item {
-        WorkDesc wd;
-        int variant;
-        double cost;
-    };
-    std::vector<Item> items;
+    std::vector<PlanItem> items;
     std::vector<int> read_of;
     FlushRec *f = new FlushRec();
     struct Update {  // host state advanced only once the flush is launched
@@ -384,7 +379,7 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
             ServeCand &sc = rd.cands[c];
             if (!rd.signal_done)
                 sig.push_back(sc.sig);
-            Item it;
+            PlanItem it;
             memset(&it.wd, 0, sizeof(WorkDesc));
             WorkDesc &wd = it.wd;
             wd.ev_off = ev_off;
@@ -422,6 +417,7 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
             wd.a0 = sch.a0;
             wd.s_end = sch.s_end;
             it.cost = (double)sch.s_end * kVariants[it.variant][0];
+            it.cap = ring_need(wd, kVariants[it.variant][0]);
             items.push_back(it);
             read_of.push_back((int)chunk_idx);
             // the band of this piece's last row is the row above the next piece
@@ -456,14 +452,12 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
         st->pending.clear();
         return RA_OK;
     }
-    std::vector<int> order(n_items);
-    for (uint32_t x = 0; x < n_items; ++x)
-        order[x] = (int)x;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (items[x].variant != items[y].variant)
-            return items[x].variant < items[y].variant;
-        return items[x].cost > items[y].cost;
-    });
+    std::vector<int> order;
+    std::vector<ClassLaunch> classes;
+    if (!make_classes(items, order, classes)) {
+        delete f;
+        return RA_EINVAL;
+    }
     std::vector<WorkDesc> work(n_items);
     for (uint32_t x = 0; x < n_items; ++x)
         work[x] = items[order[x]].wd;
@@ -480,44 +474,10 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
     f->d_res = (rawalign_result_t *)take(sizeof(rawalign_result_t) * n_items);
     unsigned long long *d_keys = (unsigned long long *)take(sizeof(unsigned long long) * chunk_idx);
     int *d_read_of = (int *)take(sizeof(int) * n_items);
-    int *d_queue = (int *)take(sizeof(int) * (kNumVariants + 2));
+    int *d_queue = (int *)take(sizeof(int) * (kMaxClasses + 2));
     bool ok = d_ev && d_sig && d_work && f->d_res && d_keys && d_read_of && d_queue;
-    std::vector<ClassLaunch> classes;
-    if (ok) {
-        int pos = 0;
-        for (int v = 0; v < kNumVariants && ok; ++v) {
-            ClassLaunch cl;
-            cl.G = kVariants[v][0];
-            cl.HR = kVariants[v][1];
-            cl.first = pos;
-            int64_t need = 4;
-            while (pos < (int)n_items && items[order[pos]].variant == v) {
-                need = std::max<int64_t>(need, (int64_t)work[pos].dC + 2);
-                need = std::max<int64_t>(need, (int64_t)work[pos].fin_wid + cl.G + 2);
-                ++pos;
-            }
-            cl.count = pos - cl.first;
-            if (cl.count == 0)
-                continue;
-            cl.max_cost = items[order[cl.first]].cost;
-            cl.ring_cap = next_pow2(need);
-            const int gpb = kBlock / cl.G;
-            size_t smem = (size_t)gpb * (cl.ring_cap + 1) * sizeof(float);
-            cl.ring_in_smem = smem <= 64 * 1024;
-            cl.smem = cl.ring_in_smem ? smem : 0;
-            int nb = stripe_max_blocks_per_sm(cl.G, cl.HR, kBlock, cl.smem);
-            if (nb <= 0) {
-                ok = false;
-                break;
-            }
-            cl.grid = std::max(1, std::min(h->sm_count * nb, (cl.count + gpb - 1) / gpb));
-            if (!cl.ring_in_smem) {
-                cl.gring = (float *)take(sizeof(float) * (uint64_t)cl.grid * gpb * cl.ring_cap);
-                ok = cl.gring != nullptr;
-            }
-            classes.push_back(cl);
-        }
-    }
+    if (ok)
+        ok = finalize_classes(h->sm_count, classes, take) == RA_OK;
     // pinned staging: inputs in one buffer, results in another
     const size_t b_ev = sizeof(float) * ev.size(), b_sig = sizeof(SigDesc) * sig.size();
     const size_t b_work = sizeof(WorkDesc) * n_items, b_rd = sizeof(int) * n_items;
@@ -550,7 +510,7 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
     RA_CUDA(cudaMemcpyAsync(d_work, hin + o_work, b_work, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(d_read_of, hin + o_rd, b_rd, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemsetAsync(d_keys, 0, sizeof(unsigned long long) * chunk_idx, s));
-    RA_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int) * (kNumVariants + 2), s));
+    RA_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int) * (kMaxClasses + 2), s));
     float *abase = (float *)h->arena.base;
     if (!sig.empty())
         RA_CUDA(launch_expected_signal(d_sig, (int)sig.size(), h->d_ref, h->d_pore, h->cfg.k, abase, s));
@@ -574,7 +534,7 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
         p.ring_in_smem = cl.ring_in_smem;
         p.b_match = h->cfg.b_match;
         p.end_free = 1;
-        p.err = d_queue + kNumVariants;
+        p.err = d_queue + kMaxClasses;
         RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
         RA_CUDA(cudaEventRecord(h->join[ci], cs));
         RA_CUDA(cudaStreamWaitEvent(s, h->join[ci], 0));

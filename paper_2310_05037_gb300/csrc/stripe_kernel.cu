@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
             if (MASKM == MASK_BITS) {
                 const int hiN = min(max(Bq + 1, 0), nvalid);
                 const int loN = min(max(Aq, 0), HR);
-                unsigned M = (1u << max(hiN, loN)) - (1u << loN);
+                unsigned M = (unsigned)((1ull << max(hiN, loN)) - (1ull << loN));
                 M = ((unsigned)j <= (unsigned)colmax) ? M : 0u;
 #pragma unroll
                 for (int r = 0; r < HR; ++r)
@@ -487,8 +487,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
             float nn = upv, nw = diag;
 #pragma unroll
             for (int r = 0; r < HR; ++r) {
-                const float dd = fabsf(__fsub_rn(eg[r], rj));
-                const float v = __fadd_rn(dd, min3f(nw, nn, D[r]));
+                const float v = __fadd_rn(fabsf(__fsub_rn(eg[r], rj)), min3f(nw, nn, D[r]));
                 nw = D[r];
                 D[r] = v;
                 nn = v;
