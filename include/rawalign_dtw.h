@@ -60,8 +60,8 @@ enum { RA_END_GLOBAL = 0, RA_END_FREE = 1 };            /* end of the DTW */
 enum { RA_UNMAPPED = 0, RA_MAPPED = 1, RA_PENDING = 2 };/* decision */
 /* kernel choice: AUTO picks a striped variant per alignment; PLAIN runs one
  * alignment per launch; RA_KERNEL_VARIANT0 + v forces striped variant v for
- * every alignment (tuning and tests): v = 0..5 are (lanes per alignment, rows
- * per lane) = (32,16) (16,16) (32,8) (16,8) (8,8) (4,8). */
+ * every alignment (tuning and tests): v = 0..8 are (lanes per alignment, rows
+ * per lane) = (32,16) (16,16) (32,8) (16,8) (8,8) (4,8) (16,24) (8,24) (32,24). */
 enum { RA_KERNEL_AUTO = 0, RA_KERNEL_PLAIN = 1, RA_KERNEL_VARIANT0 = 16 };
 
 typedef struct {
@@ -176,6 +176,7 @@ typedef struct {
     double dtw_ms;             /* CUDA-event time of the DTW kernel(s) */
     double total_ms;           /* CUDA-event time of the whole path */
     uint64_t cells;            /* in-band cells of the batch */
+    uint64_t slots;            /* lane-cell slots the plan occupies (>= cells) */
     uint32_t launches;         /* kernels launched by one run */
     uint32_t pad;
 } rawalign_dtw_stats_t;
@@ -205,6 +206,14 @@ int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_events, const f
                                uint32_t m, int32_t band_w, int64_t slope_num, int64_t slope_den,
                                int32_t end_mode, float b_match, rawalign_result_t *d_result,
                                void *cuda_stream);
+
+/* Relative cost of one lane-cell slot for each striped variant (n must be the
+ * number of variants, 9: same order as RA_KERNEL_VARIANT0 + v).  The planner
+ * picks, per alignment, the variant with the fewest cost-weighted slots; the
+ * autotuner measures these costs.  config.autotune_path may name a text file
+ * of "G HR cost" lines with the same numbers.  Returns RA_EINVAL for a wrong
+ * count or a non-positive cost. */
+int rawalign_dtw_set_variant_costs(rawalign_dtw_t *h, const double *costs, uint32_t n);
 
 /* Bytes of arena a batch of this shape needs (planning aid for callers). */
 uint64_t rawalign_dtw_batch_bytes(uint64_t n_events, uint32_t n_reads, uint32_t n_cands,

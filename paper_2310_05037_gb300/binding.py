@@ -22,7 +22,7 @@ RA_END_GLOBAL, RA_END_FREE = 0, 1
 RA_UNMAPPED, RA_MAPPED, RA_PENDING = 0, 1, 2
 RA_KERNEL_AUTO, RA_KERNEL_PLAIN = 0, 1
 RA_KERNEL_VARIANT0 = 16
-VARIANTS = [(32, 16), (16, 16), (32, 8), (16, 8), (8, 8), (4, 8)]
+VARIANTS = [(32, 16), (16, 16), (32, 8), (16, 8), (8, 8), (4, 8), (16, 24), (8, 24), (32, 24)]
 RA_KERNEL_STRIPE = {gh: RA_KERNEL_VARIANT0 + v for v, gh in enumerate(VARIANTS)}
 
 STATUS_NAMES = {0: "RA_OK", -1: "RA_EINVAL", -2: "RA_ENOMEM", -3: "RA_EAGAIN", -4: "RA_ENOTREADY",
@@ -88,6 +88,7 @@ class Stats(C.Structure):
         ("dtw_ms", C.c_double),
         ("total_ms", C.c_double),
         ("cells", C.c_uint64),
+        ("slots", C.c_uint64),
         ("launches", C.c_uint32),
         ("pad", C.c_uint32),
     ]
@@ -116,6 +117,7 @@ SIGNATURES = {
     "rawalign_dtw_destroy": (C.c_int, [C.c_void_p]),
     "rawalign_dtw_batch_stats": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Stats)]),
     "rawalign_dtw_batch_bytes": (C.c_uint64, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64]),
+    "rawalign_dtw_set_variant_costs": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_uint32]),
     "rawalign_dtw_align_noalloc": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_int32, C.c_int64,
                                              C.c_int64, C.c_int32, C.c_float, C.c_void_p, C.c_void_p]),
 }
@@ -227,6 +229,11 @@ def rawalign_dtw_batch_stats(h, batch: int) -> Stats:
     return s
 
 
+def rawalign_dtw_set_variant_costs(h, costs) -> None:
+    arr = (C.c_double * len(costs))(*[float(c) for c in costs])
+    _check("rawalign_dtw_set_variant_costs", load().rawalign_dtw_set_variant_costs(h, arr, len(costs)))
+
+
 def rawalign_dtw_batch_bytes(n_events, n_reads, n_cands, total_ref_values) -> int:
     return int(load().rawalign_dtw_batch_bytes(int(n_events), int(n_reads), int(n_cands), int(total_ref_values)))
 
@@ -254,7 +261,7 @@ class Aligner:
 
     def __init__(self, pore, ref2bit, ref_len, arena_bytes=1 << 30, k=6, b_match=0.4, score_threshold=20.0,
                  end_mode=RA_END_GLOBAL, kernel=RA_KERNEL_AUTO, stream=None, serve_slots=0,
-                 serve_max_events=0, max_candidates=64, device="cuda:0"):
+                 serve_max_events=0, max_candidates=64, device="cuda:0", autotune_path=None):
         import torch
 
         self.torch = torch
@@ -274,7 +281,8 @@ class Aligner:
         cfg.kernel = kernel
         cfg.serve_slots = serve_slots
         cfg.serve_max_events = serve_max_events
-        cfg.autotune_path = None
+        self._tune_path = autotune_path.encode() if autotune_path else None
+        cfg.autotune_path = self._tune_path
         self.cfg = cfg
         self.h = rawalign_dtw_create(cfg, pore, ref2bit, ref_len)
 

@@ -94,13 +94,14 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
             it.variant = b.plain ? 0 : forced;
             s = schedule(band, 0, n, kVariants[it.variant][0], kVariants[it.variant][1]);
         } else {
-            it.variant = choose_variant(band, 0, n, s);
+            it.variant = choose_variant(band, 0, n, s, h->slot_cost);
         }
         wd.dC = s.dC;
         wd.a0 = s.a0;
         wd.s_end = s.s_end;
         it.cost = (double)s.s_end * kVariants[it.variant][0];
         it.cap = ring_need(wd, kVariants[it.variant][0]);
+        b.slots += (uint64_t)std::max(s.s_end, 0) * kVariants[it.variant][0] * kVariants[it.variant][1];
         b.max_rows = std::max<int>(b.max_rows, (int)n);
         sig[c].ref_off = cd.ref_offset;
         sig[c].r_off = r_total;
@@ -303,6 +304,23 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
     if (!h)
         return RA_ENOMEM;
     h->cfg = *config;
+    for (int v = 0; v < kNumVariants; ++v)
+        h->slot_cost[v] = kSlotCost[v];
+    if (config->autotune_path) {
+        // lines "G HR cost": the measured relative cost of one lane-cell slot
+        FILE *f = fopen(config->autotune_path, "r");
+        if (!f) {
+            delete h;
+            return RA_EINVAL;
+        }
+        int G, HR;
+        double c;
+        while (fscanf(f, "%d %d %lf", &G, &HR, &c) == 3)
+            for (int v = 0; v < kNumVariants; ++v)
+                if (kVariants[v][0] == G && kVariants[v][1] == HR && c > 0 && std::isfinite(c))
+                    h->slot_cost[v] = c;
+        fclose(f);
+    }
     h->cfg.autotune_path = nullptr;
     if (const char *mm = getenv("RAWALIGN_MASK_MODE"))
         set_mask_mode(strcmp(mm, "rowcmp") == 0 ? 0 : 1);
@@ -503,6 +521,7 @@ extern "C" int rawalign_dtw_batch_stats(rawalign_dtw_t *h, uint64_t batch, rawal
     out->dtw_ms = ms;
     out->total_ms = tot;
     out->cells = b.cells;
+    out->slots = b.slots;
     out->launches = b.launches;
     out->pad = 0;
     return RA_OK;
@@ -545,6 +564,18 @@ extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
     if (h->fork)
         cudaEventDestroy(h->fork);
     delete h;
+    return RA_OK;
+}
+
+extern "C" int rawalign_dtw_set_variant_costs(rawalign_dtw_t *h, const double *costs, uint32_t n)
+{
+    if (!h || !costs || n != (uint32_t)kNumVariants)
+        return RA_EINVAL;
+    for (int v = 0; v < kNumVariants; ++v)
+        if (!(costs[v] > 0) || !std::isfinite(costs[v]))
+            return RA_EINVAL;
+    for (int v = 0; v < kNumVariants; ++v)
+        h->slot_cost[v] = costs[v];
     return RA_OK;
 }
 

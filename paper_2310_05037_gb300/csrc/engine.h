@@ -24,9 +24,13 @@ namespace ra_host {
 constexpr int kBlock = 128;
 // (lanes per alignment, rows per lane); the cost factor is the relative issue
 // cost of one lane-cell slot (more rows per lane amortise the per-step work).
-const int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}};
-const double kSlotCost[] = {1.0, 1.0, 1.25, 1.25, 1.25, 1.25};
-constexpr int kNumVariants = 6;
+// Relative cost of one lane-cell slot per variant: the autotuner's
+// measurement on a GB300 (each variant on a batch shaped for its steady
+// state; 8 rows per lane pay the per-step overhead over fewer cells, 24 rows
+// amortise it further).  rawalign_dtw_set_variant_costs replaces them.
+const int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}, {16, 24}, {8, 24}, {32, 24}};
+const double kSlotCost[] = {1.2093, 1.2136, 1.8288, 1.8509, 1.8823, 2.0006, 1.0036, 1.0227, 1.0};
+constexpr int kNumVariants = 9;
 constexpr int kMaxClasses = 64;              // launches per run (variant x ring size)
 constexpr size_t kSmemRingLimit = 96 * 1024; // larger rings go to global memory
 
@@ -182,6 +186,7 @@ struct ClassLaunch {
 };
 
 struct Batch {
+    uint64_t slots = 0;          // planned lane-cell slots (sum of steps x G x HR)
     uint32_t n_reads = 0, n_cands = 0;
     uint64_t n_events = 0;
     std::vector<void *> blocks;  // arena allocations
@@ -239,6 +244,7 @@ struct rawalign_dtw {
     std::map<uint64_t, Ticket> tickets;
     int max_blocks[kNumVariants][2] = {};
     ServeState *serve = nullptr;       // Read-Until serving state (serve.cu)
+    double slot_cost[kNumVariants] = {};  // relative cost of a lane-cell slot per variant
 };
 
 
@@ -269,7 +275,7 @@ inline int next_pow2(int64_t x)
 
 // Chooses the striped variant for one piece of an alignment: most in-band
 // cells per unit of issue cost, ties to the earlier (wider) variant.
-inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &out)
+inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &out, const double *cost = kSlotCost)
 {
     int best = -1;
     double best_score = -1;
@@ -280,7 +286,7 @@ inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &o
             out = s;
             return 0;
         }
-        const double score = s.eff / kSlotCost[v] * (1.0 + 0.02 * (kNumVariants - v));
+        const double score = s.eff / cost[v] * (1.0 + 0.02 * (kNumVariants - v));
         if (score > best_score) {
             best_score = score;
             best = v;
@@ -346,7 +352,11 @@ inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &o
 inline int ring_need(const WorkDesc &wd, int G)
 {
     int64_t need = std::max<int64_t>((int64_t)wd.dC + 2, (int64_t)wd.fin_wid + G + 2);
-    return next_pow2(std::max<int64_t>(need, 128));
+    // sizes in powers of four (128, 512, 2048, ...): few launch classes
+    int64_t cap = 128;
+    while (cap < need)
+        cap <<= 2;
+    return (int)cap;
 }
 
 // Launch geometry of each class: ring in shared memory when it fits, grid of

@@ -411,7 +411,7 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
                 it.variant = 0;
                 sch.s_end = 0;
             } else {
-                it.variant = choose_variant(sc.band, row0, nrows, sch);
+                it.variant = choose_variant(sc.band, row0, nrows, sch, h->slot_cost);
             }
             wd.dC = sch.dC;
             wd.a0 = sch.a0;

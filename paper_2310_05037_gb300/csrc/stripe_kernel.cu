@@ -472,9 +472,12 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
             }
             float eg[HR];
             if (MASKM == MASK_BITS) {
-                const int hiN = min(max(Bq + 1, 0), nvalid);
-                const int loN = min(max(Aq, 0), HR);
-                unsigned M = (unsigned)((1ull << max(hiN, loN)) - (1ull << loN));
+                // rows [loN, hiN) are in band: one bit-field mask instruction
+                const int loN = max(Aq, 0);
+                const int hiN = min(Bq + 1, nvalid);
+                const int width = max(hiN - loN, 0);
+                unsigned M;
+                asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(M) : "r"(loN), "r"(width));
                 M = ((unsigned)j <= (unsigned)colmax) ? M : 0u;
 #pragma unroll
                 for (int r = 0; r < HR; ++r)
@@ -545,6 +548,9 @@ static void *pick_stripe(int G, int HR, bool freeend, bool smem_ring)
     }
     RA_PICK(32, 16)
     RA_PICK(16, 16)
+    RA_PICK(32, 24)
+    RA_PICK(16, 24)
+    RA_PICK(8, 24)
     RA_PICK(32, 8)
     RA_PICK(16, 8)
     RA_PICK(8, 8)
