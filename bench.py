@@ -1,13 +1,15 @@
 """Benchmark of the RawAlign DTW alignment path on GB300.
 
-One step = one pass of the whole path over the batched-uneven workload
-(20k reads with lognormal event counts, 1-8 candidate regions each on a
-100 Mb reference, band 10 % of the span): expected signal, band, DTW, end
-cell, score and per-read decision, all in the library's kernels (one CUDA
-graph replay).  Inputs are resident in HBM when the timed region starts and
+One step = one pass of the whole path over one batch: by default the
+batched-uneven workload (20k reads with lognormal event counts, 1-8
+candidate regions each on a 100 Mb reference, band 10 % of the span);
+--workload readuntil | longread | plain picks another full-size batch.  The
+path is expected signal, band, DTW, end cell, score and per-read decision,
+all in the library's kernels (replays of the captured CUDA graphs).  Inputs are resident in HBM when the timed region starts and
 are larger than L2; L2 is also flushed between timed steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload batched|readuntil|longread|plain]
 
 Prints one JSON line (rank 0).  value = in-band DTW cells / device time
 (GCUPS, whole job over all ranks).  e2e = the same metric through the public
@@ -31,9 +33,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = ("batched_uneven: 20000 reads, lognormal event counts (median 1500, 200-8000), 1-8 candidates "
-            "per read (1 true + decoys) on a 100 Mb uniform-ACGT reference, span = events x U(0.9,1.3), "
-            "band 10% of span, 6-mer pore table N(0,1), noise sd 0.3, 5% skips, FP32 global DTW")
+WORKLOADS = {
+    "batched": ("batched_uneven: %d reads, lognormal event counts (median 1500, 200-8000), 1-8 candidates "
+                "per read (1 true + decoys) on a 100 Mb uniform-ACGT reference, span = events x U(0.9,1.3), "
+                "band 10%% of span, 6-mer pore table N(0,1), noise sd 0.3, 5%% skips, FP32 global DTW"),
+    "readuntil": ("readuntil_prefix: 100000 reads x first 450 events, 16-64 candidates per read on a 3 Gb "
+                  "uniform-ACGT reference with 2% of its 5 kb blocks duplicated at 90% identity, band 64, "
+                  "FP32 global DTW"),
+    "longread": ("longread_banded: 2000 reads of 20k-100k events (uniform), 2 candidates each on a 100 Mb "
+                 "reference, band 5% of span, 5% skips + 5% stays, noise sd 0.4, FP32 global DTW"),
+    "plain": ("plain: 64 reads x 500 events, 1 candidate each (true 550-value segment of a 20 kb reference), "
+              "unbanded FP32 DTW"),
+}
 METRIC = "DTW GCUPS and reads/s (batched and served vs plain per-alignment kernel); p50/p99 chunk latency"
 OPS_PER_CELL = 4  # sub, min, min, add per DP cell
 
@@ -121,26 +132,24 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _all_reduce(x, world, op_name):
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=getattr(dist.ReduceOp, op_name))
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    return _all_reduce(x, world, "MAX")
 
 
 def sum_over_ranks(x, world):
-    if world <= 1:
-        return x
-    import torch
-    import torch.distributed as dist
-
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _all_reduce(x, world, "SUM")
 
 
 def cpu_baseline(w, seconds=15.0, seed=1):
@@ -168,13 +177,26 @@ def cpu_baseline(w, seconds=15.0, seed=1):
                       % (done, cells, el), "seconds": el}
 
 
+def workload_name(args):
+    d = WORKLOADS[args.workload]
+    return d % args.reads if args.workload == "batched" else d
+
+
+def make_workload(S, args, rank):
+    """The step's batch; every rank draws its own (weak scaling, replicas)."""
+    if args.workload == "batched":
+        return S.config_batched(n_reads=args.reads, seed=0x5EED0002 + rank)
+    return S.scaled(args.workload, "full", seed=None if rank == 0 else 0x5EED1000 + rank)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--reads", type=int, default=20000)
+    ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
+    ap.add_argument("--reads", type=int, default=20000, help="reads of the batched workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -199,7 +221,7 @@ def main():
     __graft_entry__.build()
     from paper_2310_05037_gb300 import binding as B
 
-    w = S.config_batched(n_reads=args.reads, seed=0x5EED0002 + rank)
+    w = make_workload(S, args, rank)
     m_total = int(np.sum(w.cands["ref_len_bases"].astype(np.int64) - w.k + 1))
     need = B.rawalign_dtw_batch_bytes(len(w.events), w.n_reads, w.n_cands, m_total)
     arena = 2 * need + len(w.ref2bit) + (256 << 20)
@@ -265,7 +287,8 @@ def main():
         "metric": METRIC, "value": round(value, 2), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "reads": w.n_reads, "alignments": w.n_cands, "cells_per_step": cells_step,
+        "config": {"workload": workload_name(args), "reads": w.n_reads, "alignments": w.n_cands,
+                   "cells_per_step": cells_step,
                    "l2": "inputs larger than L2 (expected signal %.0f MB, events %.0f MB) and a 256 MB L2 flush "
                          "between timed steps" % (m_total * 4 / 1e6, len(w.events) * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -277,8 +300,14 @@ def main():
 
     # plain one-alignment-per-launch kernel on a sample of the same workload
     if not args.no_plain and rank == 0:
+        # a random sample of the workload's alignments: at most 300, and no
+        # more than about 1e9 table cells (seconds for the plain kernel)
         rng = np.random.default_rng(5)
-        sub = w.subset(np.sort(rng.choice(w.n_cands, size=min(300, w.n_cands), replace=False)))
+        perm = rng.permutation(w.n_cands)[:300]
+        nn = w.read_lengths()[w.cands["read_id"][perm].astype(np.int64)]
+        mm = w.cands["ref_len_bases"][perm].astype(np.int64) - w.k + 1
+        keep = max(1, int(np.searchsorted(np.cumsum(nn * mm), 1e9)))
+        sub = w.subset(np.sort(perm[:keep]))
         alp = B.Aligner(sub.pore, sub.ref2bit, sub.ref_len, arena_bytes=1 << 30, kernel=B.RA_KERNEL_PLAIN,
                         device="cuda:%d" % local)
         bp = alp.prepare(sub.events, sub.read_offsets, sub.cands)
@@ -356,7 +385,7 @@ def run_reference(args, S):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = S.config_batched(n_reads=args.reads)
+    w = make_workload(S, args, 0)
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup):
         cpu_baseline(w, seconds=per_step, seed=100 + i)
@@ -371,7 +400,7 @@ def run_reference(args, S):
         "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GCUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(secs), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "reads": w.n_reads, "alignments": w.n_cands},
+        "config": {"workload": workload_name(args), "reads": w.n_reads, "alignments": w.n_cands},
         "cpu_baseline": {"value": round(value, 5), "unit": "GCUPS", "cores": 1, "kind": "oracle",
                          "sample": "each step: random alignments of the workload for %.1f s, single thread; "
                                    "last: %s" % (per_step, samples[-1])},

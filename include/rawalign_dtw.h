@@ -215,7 +215,13 @@ int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_events, const f
  * count or a non-positive cost. */
 int rawalign_dtw_set_variant_costs(rawalign_dtw_t *h, const double *costs, uint32_t n);
 
-/* Bytes of arena a batch of this shape needs (planning aid for callers). */
+/* Bytes of arena a batch of this shape needs (planning aid for callers).
+ * Not included: ring scratch for alignments whose band is too wide for the
+ * shared-memory ring (about 2w+1 > 2000 columns).  Those take it from the
+ * arena's remaining free space, up to (blocks x groups per block x ring
+ * entries x 4) bytes per launch class; with less free space their class runs
+ * on fewer blocks (slower, same results), and RA_ENOMEM comes back only when
+ * not even one block's ring fits. */
 uint64_t rawalign_dtw_batch_bytes(uint64_t n_events, uint32_t n_reads, uint32_t n_cands,
                                   uint64_t total_ref_values);
 

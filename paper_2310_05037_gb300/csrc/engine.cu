@@ -96,12 +96,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         } else {
             it.variant = choose_variant(band, 0, n, s, h->slot_cost);
         }
-        wd.dC = s.dC;
-        wd.a0 = s.a0;
-        wd.s_end = s.s_end;
-        it.cost = (double)s.s_end * kVariants[it.variant][0];
-        it.cap = ring_need(wd, kVariants[it.variant][0]);
-        b.slots += (uint64_t)std::max(s.s_end, 0) * kVariants[it.variant][0] * kVariants[it.variant][1];
+        set_schedule(it, s);
         b.max_rows = std::max<int>(b.max_rows, (int)n);
         sig[c].ref_off = cd.ref_offset;
         sig[c].r_off = r_total;
@@ -109,6 +104,11 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         sig[c].strand = cd.strand;
         r_total += (uint64_t)m;
     }
+    if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO)
+        shorten_longest(items, h->sm_count, h->slot_cost);
+    b.slots = 0;
+    for (const PlanItem &it : items)
+        b.slots += (uint64_t)std::max(it.wd.s_end, 0) * kVariants[it.variant][0] * kVariants[it.variant][1];
     // launch order and classes (variant x ring size), longest first
     std::vector<int> order;
     b.classes.clear();

@@ -304,6 +304,62 @@ struct PlanItem {
     double cost = 0;    // lane-steps: longest first
 };
 
+inline int ring_need(const WorkDesc &wd, int G);
+
+inline void set_schedule(PlanItem &it, const Sched &s)
+{
+    it.wd.dC = s.dC;
+    it.wd.a0 = s.a0;
+    it.wd.s_end = s.s_end;
+    it.cost = (double)s.s_end * kVariants[it.variant][0];
+    it.cap = ring_need(it.wd, kVariants[it.variant][0]);
+}
+
+// A batch lasts at least as long as its longest alignment on one group.  The
+// batch's length is estimated as its cost-weighted lane-cell slots spread
+// over the resident lanes (about 512 per SM).  Alignments start longest
+// first, so one whose own duration (steps x rows per lane x slot cost) stays
+// below that estimate does not set the batch's length; one above it moves to
+// the 32-lane variant with the best cost-weighted efficiency when that is
+// shorter, so one group of 32 lanes finishes it in about half the time.
+inline void shorten_longest(std::vector<PlanItem> &items, int sm_count, const double *cost)
+{
+    double total = 0;
+    for (const PlanItem &it : items)
+        total += (double)std::max(it.wd.s_end, 0) * kVariants[it.variant][0] * kVariants[it.variant][1] *
+                 cost[it.variant];
+    const double batch_len = total / (512.0 * std::max(sm_count, 1));
+    for (PlanItem &it : items) {
+        const int v0 = it.variant;
+        const double dur = (double)it.wd.s_end * kVariants[v0][1] * cost[v0];
+        if (it.wd.s_end <= 0 || kVariants[v0][0] == 32 || dur <= batch_len)
+            continue;
+        BandDef band;
+        band.num = it.wd.num;
+        band.den = it.wd.den;
+        band.w = it.wd.w;
+        band.m = it.wd.m;
+        int best = -1;
+        double best_score = -1;
+        Sched best_s;
+        for (int v = 0; v < kNumVariants; ++v) {
+            if (kVariants[v][0] != 32)
+                continue;
+            Sched s = schedule(band, it.wd.row0, it.wd.nrows, 32, kVariants[v][1]);
+            const double score = s.eff / cost[v];
+            if (s.s_end > 0 && score > best_score) {
+                best_score = score;
+                best = v;
+                best_s = s;
+            }
+        }
+        if (best < 0 || (double)best_s.s_end * kVariants[best][1] * cost[best] >= dur)
+            continue;
+        it.variant = best;
+        set_schedule(it, best_s);
+    }
+}
+
 // Sorts the items into launch order (variant, ring size, longest first) and
 // cuts them into launch classes of one variant and one ring size, so that a
 // few alignments with very wide bands do not force a large ring (and fewer
@@ -375,9 +431,13 @@ int finalize_classes(int sm_count, std::vector<ClassLaunch> &classes, Alloc allo
             return RA_EDEVICE;
         cl.grid = std::max(1, std::min(sm_count * nb, (cl.count + gpb - 1) / gpb));
         if (!cl.ring_in_smem) {
-            cl.gring = (float *)alloc(sizeof(float) * (uint64_t)cl.grid * gpb * cl.ring_cap);
-            if (!cl.gring)
-                return RA_ENOMEM;
+            // ring scratch comes from the arena's free space: with less room,
+            // fewer blocks (the persistent groups share the same queue)
+            while (!(cl.gring = (float *)alloc(sizeof(float) * (uint64_t)cl.grid * gpb * cl.ring_cap))) {
+                if (cl.grid == 1)
+                    return RA_ENOMEM;
+                cl.grid = (cl.grid + 1) / 2;
+            }
         }
     }
     return RA_OK;
