@@ -60,8 +60,9 @@ enum { RA_END_GLOBAL = 0, RA_END_FREE = 1 };            /* end of the DTW */
 enum { RA_UNMAPPED = 0, RA_MAPPED = 1, RA_PENDING = 2 };/* decision */
 /* kernel choice: AUTO picks a striped variant per alignment; PLAIN runs one
  * alignment per launch; RA_KERNEL_VARIANT0 + v forces striped variant v for
- * every alignment (tuning and tests): v = 0..8 are (lanes per alignment, rows
- * per lane) = (32,16) (16,16) (32,8) (16,8) (8,8) (4,8) (16,24) (8,24) (32,24). */
+ * every alignment (tuning and tests): v = 0..9 are (lanes per alignment, rows
+ * per lane) = (32,16) (16,16) (32,8) (16,8) (8,8) (4,8) (16,24) (8,24) (32,24)
+ * (4,24). */
 enum { RA_KERNEL_AUTO = 0, RA_KERNEL_PLAIN = 1, RA_KERNEL_VARIANT0 = 16 };
 
 typedef struct {
@@ -208,7 +209,7 @@ int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_events, const f
                                void *cuda_stream);
 
 /* Relative cost of one lane-cell slot for each striped variant (n must be the
- * number of variants, 9: same order as RA_KERNEL_VARIANT0 + v).  The planner
+ * number of variants, 10: same order as RA_KERNEL_VARIANT0 + v).  The planner
  * picks, per alignment, the variant with the fewest cost-weighted slots; the
  * autotuner measures these costs.  config.autotune_path may name a text file
  * of "G HR cost" lines with the same numbers.  Returns RA_EINVAL for a wrong

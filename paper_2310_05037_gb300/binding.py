@@ -22,7 +22,7 @@ RA_END_GLOBAL, RA_END_FREE = 0, 1
 RA_UNMAPPED, RA_MAPPED, RA_PENDING = 0, 1, 2
 RA_KERNEL_AUTO, RA_KERNEL_PLAIN = 0, 1
 RA_KERNEL_VARIANT0 = 16
-VARIANTS = [(32, 16), (16, 16), (32, 8), (16, 8), (8, 8), (4, 8), (16, 24), (8, 24), (32, 24)]
+VARIANTS = [(32, 16), (16, 16), (32, 8), (16, 8), (8, 8), (4, 8), (16, 24), (8, 24), (32, 24), (4, 24)]
 RA_KERNEL_STRIPE = {gh: RA_KERNEL_VARIANT0 + v for v, gh in enumerate(VARIANTS)}
 
 STATUS_NAMES = {0: "RA_OK", -1: "RA_EINVAL", -2: "RA_ENOMEM", -3: "RA_EAGAIN", -4: "RA_ENOTREADY",

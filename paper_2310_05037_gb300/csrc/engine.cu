@@ -322,8 +322,6 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
         fclose(f);
     }
     h->cfg.autotune_path = nullptr;
-    if (const char *mm = getenv("RAWALIGN_MASK_MODE"))
-        set_mask_mode(strcmp(mm, "rowcmp") == 0 ? 0 : 1);
     h->stream = (cudaStream_t)config->cuda_stream;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);

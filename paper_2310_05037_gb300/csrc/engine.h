@@ -28,9 +28,10 @@ constexpr int kBlock = 128;
 // measurement on a GB300 (each variant on a batch shaped for its steady
 // state; 8 rows per lane pay the per-step overhead over fewer cells, 24 rows
 // amortise it further).  rawalign_dtw_set_variant_costs replaces them.
-const int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}, {16, 24}, {8, 24}, {32, 24}};
-const double kSlotCost[] = {1.2093, 1.2136, 1.8288, 1.8509, 1.8823, 2.0006, 1.0036, 1.0227, 1.0};
-constexpr int kNumVariants = 9;
+const int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}, {16, 24}, {8, 24}, {32, 24},
+                           {4, 24}};
+const double kSlotCost[] = {1.2107, 1.2336, 1.8882, 1.9132, 1.9968, 2.1240, 1.0095, 1.0287, 1.0, 1.0656};
+constexpr int kNumVariants = 10;
 constexpr int kMaxClasses = 64;              // launches per run (variant x ring size)
 constexpr size_t kSmemRingLimit = 96 * 1024; // larger rings go to global memory
 

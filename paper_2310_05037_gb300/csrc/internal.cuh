@@ -73,7 +73,6 @@ cudaError_t launch_check_events(const float *ev, uint64_t n, int *err, cudaStrea
 cudaError_t launch_stripe(int G, int HR, const StripeParams &p, int grid, int block, size_t smem,
                           cudaStream_t s);
 int stripe_max_blocks_per_sm(int G, int HR, int block, size_t smem);
-void set_mask_mode(int mode);  // 0: per-row compare, 1: per-step bit mask
 cudaError_t launch_plain(const WorkDesc *w, const float *events, const float *r_all, float *diag,
                          rawalign_result_t *results, unsigned long long *best_keys, float b_match,
                          int end_free, cudaStream_t s);

@@ -20,11 +20,10 @@
 // each result, the event value of a row that is outside the band at the
 // current column is replaced by +inf, so d = |e - r| = +inf and the cell is
 // +inf whatever its neighbours are; this keeps the select off the dependent
-// min -> add chain.  Two ways to decide which rows are in band are built:
-//   MASK_ROWCMP  per row: (unsigned)(j - lo_r) <= hi_r - lo_r
-//   MASK_BITS    per step: the interval of rows in band at column j from two
-//                column-wise DDAs (first row whose band starts after j, first
-//                row whose band ends before j), as a bit mask.
+// min -> add chain.  The rows in band at column j form an interval, found
+// each step by two column-wise DDAs (first row whose band starts after j,
+// first row whose band ends before j) and turned into a bit mask by one
+// bmsk instruction.
 // The cell itself is sub, min3 (one exact 3-input min), add, in that order.
 #include <climits>
 #include <cstdint>
@@ -33,8 +32,6 @@
 #include "internal.cuh"
 
 namespace ra {
-
-enum { MASK_ROWCMP = 0, MASK_BITS = 1 };
 
 // Per-group constants of the current alignment and per-lane band state that
 // only stripe transitions read: kept in shared memory, not registers.
@@ -57,7 +54,7 @@ static __device__ __forceinline__ void st_shared_if(bool pred, float *addr, floa
                  :: "r"((int)pred), "r"(a), "f"(v) : "memory");
 }
 
-template <int G, int HR, bool FREE_END, int MASKM, bool RING_SMEM>
+template <int G, int HR, bool FREE_END, bool RING_SMEM>
 __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
 {
     constexpr int H = G * HR;
@@ -93,7 +90,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         lo[r] = kBigCol;
         wid[r] = 0;
     }
-    // column-wise DDA (MASK_BITS): rows in band at column j are [Aq, Bq]
+    // column-wise DDA: rows in band at column j are [Aq, Bq]
     // relative to the lane's first row
     int Bq = -BIGROW, Br = 0, Aq = BIGROW, Ar = 0, cq = 0, cr = 0, cnum = 1;
     int nvalid = 0, colmax = -1;
@@ -290,7 +287,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                         bestj = -1;
                         k = 0;
                         j = wd.a0 - 1 - t;  // first column of this lane
-                        if (MASKM == MASK_BITS) {
+                        {
                             if (num == 0) {
                                 Bq = BIGROW;
                                 Aq = -BIGROW;
@@ -367,7 +364,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
 #pragma unroll 2
         for (int q = 0; q < nstep; ++q) {
             ++j;
-            if (MASKM == MASK_BITS) {
+            {
                 Bq += cq;
                 Br += cr;
                 if (Br >= cnum) {
@@ -435,7 +432,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                     lc->hiR = R;
                     setup_stripe();
                     j -= gc->dC;
-                    if (MASKM == MASK_BITS) {
+                    {
                         const int qdC = gc->qdC, rdC = gc->rdC;
                         Bq -= H + qdC;
                         Br -= rdC;
@@ -471,7 +468,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                 rjn = __ldg(rr + jc);
             }
             float eg[HR];
-            if (MASKM == MASK_BITS) {
+            {
                 // rows [loN, hiN) are in band: one bit-field mask instruction
                 const int loN = max(Aq, 0);
                 const int hiN = min(Bq + 1, nvalid);
@@ -482,10 +479,6 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
 #pragma unroll
                 for (int r = 0; r < HR; ++r)
                     eg[r] = ((M >> r) & 1u) ? e[r] : kInf;
-            } else {
-#pragma unroll
-                for (int r = 0; r < HR; ++r)
-                    eg[r] = ((unsigned)(j - lo[r]) <= wid[r]) ? e[r] : kInf;
             }
             float nn = upv, nw = diag;
 #pragma unroll
@@ -525,32 +518,23 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
 // ---------------------------------------------------------------------------
 // variant table and launchers
 // ---------------------------------------------------------------------------
-template <int G, int HR, bool F, int M>
+template <int G, int HR, bool F>
 static void *stripe_fn(bool smem_ring)
 {
-    return smem_ring ? (void *)dtw_stripe_kernel<G, HR, F, M, true> : (void *)dtw_stripe_kernel<G, HR, F, M, false>;
+    return smem_ring ? (void *)dtw_stripe_kernel<G, HR, F, true> : (void *)dtw_stripe_kernel<G, HR, F, false>;
 }
-
-static int g_mask_mode = MASK_BITS;
-
-void set_mask_mode(int mode) { g_mask_mode = mode; }
 
 static void *pick_stripe(int G, int HR, bool freeend, bool smem_ring)
 {
-    const int mm = g_mask_mode;
 #define RA_PICK(g, h)                                                                              \
-    if (G == g && HR == h) {                                                                       \
-        if (mm == MASK_BITS)                                                                       \
-            return freeend ? stripe_fn<g, h, true, MASK_BITS>(smem_ring)                          \
-                           : stripe_fn<g, h, false, MASK_BITS>(smem_ring);                        \
-        return freeend ? stripe_fn<g, h, true, MASK_ROWCMP>(smem_ring)                            \
-                       : stripe_fn<g, h, false, MASK_ROWCMP>(smem_ring);                          \
-    }
+    if (G == g && HR == h)                                                                         \
+        return freeend ? stripe_fn<g, h, true>(smem_ring) : stripe_fn<g, h, false>(smem_ring);
     RA_PICK(32, 16)
     RA_PICK(16, 16)
     RA_PICK(32, 24)
     RA_PICK(16, 24)
     RA_PICK(8, 24)
+    RA_PICK(4, 24)
     RA_PICK(32, 8)
     RA_PICK(16, 8)
     RA_PICK(8, 8)
