@@ -22,31 +22,54 @@
 namespace ra {
 
 // ---------------------------------------------------------------------------
-// a1: expected signal.  One warp per candidate region; each lane forms the
-// k-mer index of its own columns from the packed reference.
+// a1: expected signal.  One warp per candidate region, one column per lane
+// (coalesced stores).  The reference is read as 32-bit words of 16 bases
+// (base q of a word in bits 2q, 2q+1), so the k bases from position p are
+// bits 2(p mod 16) .. 2(p mod 16)+2k-1 of the word pair at p/16: one funnel
+// shift.  That window holds the bases with the first one in the LOWEST
+// digit.  Forward strand: the k-mer index wants the first base in the
+// highest digit, so the digits are reversed (bit reverse, then swap the two
+// bits of each digit).  Reverse strand: the k-mer at column j of the reverse
+// complement starts from the base at end-1-j and walks backwards, so its
+// index is exactly the complemented window at end-k-j (first base lowest).
+// The pore table is staged in shared memory when it has at most 4096 entries.
 // ---------------------------------------------------------------------------
-__global__ void expected_signal_kernel(const SigDesc *__restrict__ d, int n,
-                                       const uint8_t *__restrict__ ref2bit,
-                                       const float *__restrict__ pore, int k,
-                                       float *__restrict__ r_all)
+static __device__ __forceinline__ unsigned reverse_digits(unsigned w, int k)
 {
+    const unsigned y = __brev(w) >> (32 - 2 * k);
+    return ((y & 0x55555555u) << 1) | ((y >> 1) & 0x55555555u);
+}
+
+template <bool SMEM_TABLE>
+__global__ void __launch_bounds__(256) expected_signal_kernel(const SigDesc *__restrict__ d, int n,
+                                                              const uint32_t *__restrict__ ref32,
+                                                              const float *__restrict__ pore, int k,
+                                                              float *__restrict__ r_all)
+{
+    extern __shared__ float table_s[];
+    const float *table = pore;
+    if (SMEM_TABLE) {
+        const int nt = 1 << (2 * k);
+        for (int x = threadIdx.x; x < nt; x += blockDim.x)
+            table_s[x] = __ldg(pore + x);
+        __syncthreads();
+        table = table_s;
+    }
+    const unsigned kmask = (1u << (2 * k)) - 1u;  // k <= 8
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n; c += nwarps) {
         const SigDesc sd = d[c];
         const int64_t m = (int64_t)sd.len - k + 1;
         float *out = r_all + sd.r_off;
+        const uint64_t last = sd.ref_off + sd.len - (uint64_t)k;  // window start of the reverse strand's column 0
         for (int64_t j = lane; j < m; j += 32) {
-            unsigned idx = 0;
-            for (int q = 0; q < k; ++q) {
-                uint64_t pos = sd.strand ? sd.ref_off + sd.len - 1 - (uint64_t)(j + q)
-                                         : sd.ref_off + (uint64_t)(j + q);
-                unsigned code = (__ldg(ref2bit + (pos >> 2)) >> ((pos & 3) * 2)) & 3u;
-                if (sd.strand)
-                    code = 3u - code;
-                idx = idx * 4u + code;
-            }
-            out[j] = __ldg(pore + idx);
+            const uint64_t p = sd.strand ? last - (uint64_t)j : sd.ref_off + (uint64_t)j;
+            const uint64_t wi = p >> 4;
+            const unsigned lo = __ldg(ref32 + wi), hi = __ldg(ref32 + wi + 1);
+            const unsigned win = __funnelshift_r(lo, hi, 2u * (unsigned)(p & 15)) & kmask;
+            const unsigned idx = sd.strand ? (win ^ kmask) : reverse_digits(win, k);
+            out[j] = table[idx];
         }
     }
 }
@@ -192,9 +215,14 @@ cudaError_t launch_expected_signal(const SigDesc *d, int n, const uint8_t *ref2b
     if (n <= 0)
         return cudaSuccess;
     int blocks = (n + 7) / 8;
-    if (blocks > 152 * 16)
-        blocks = 152 * 16;
-    expected_signal_kernel<<<blocks, 256, 0, s>>>(d, n, ref2bit, pore, k, r_all);
+    if (blocks > 152 * 8)
+        blocks = 152 * 8;
+    const uint32_t *ref32 = (const uint32_t *)ref2bit;  // 256-byte aligned, padded by 16 bytes
+    if (k <= 6) {
+        expected_signal_kernel<true><<<blocks, 256, sizeof(float) << (2 * k), s>>>(d, n, ref32, pore, k, r_all);
+    } else {
+        expected_signal_kernel<false><<<blocks, 256, 0, s>>>(d, n, ref32, pore, k, r_all);
+    }
     return cudaGetLastError();
 }
 

@@ -338,7 +338,9 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
     }
     h->arena.init(config->arena_dev, config->arena_bytes);
     h->d_pore = (float *)h->arena.alloc(sizeof(float) * n_pore);
-    h->d_ref = (uint8_t *)h->arena.alloc(std::max<uint64_t>((ref_len + 3) / 4, 1));
+    // 16 bytes of zero padding: the expected-signal kernel reads the packed
+    // reference as pairs of 32-bit words
+    h->d_ref = (uint8_t *)h->arena.alloc((ref_len + 3) / 4 + 16);
     if (!h->d_pore || !h->d_ref) {
         delete h;
         return RA_ENOMEM;
@@ -347,6 +349,7 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
     int rc = RA_OK;
     if (cudaMemcpyAsync(h->d_pore, pore_model, sizeof(float) * n_pore, cudaMemcpyHostToDevice, h->stream) !=
             cudaSuccess ||
+        cudaMemsetAsync(h->d_ref + (ref_len + 3) / 4, 0, 16, h->stream) != cudaSuccess ||
         (ref_len && cudaMemcpyAsync(h->d_ref, ref_2bit, (ref_len + 3) / 4, cudaMemcpyHostToDevice, h->stream) !=
                         cudaSuccess) ||
         cudaStreamSynchronize(h->stream) != cudaSuccess)

@@ -115,3 +115,24 @@ def test_arena_too_small():
         finally:
             al.close()
     assert ei.value.code == B.RA_ENOMEM
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 6, 7, 8])
+def test_kmer_lengths_and_word_offsets(k):
+    """Expected signal (Sup. A.1.1) for every supported k, both strands, with
+    regions starting at every base offset within a packed 16-base word and
+    ending at the reference's last base."""
+    rng = np.random.default_rng(100 + k)
+    pore = rng.standard_normal(4 ** k).astype(np.float32)
+    ref_len = 4099
+    ref = S.hashed_reference(k, ref_len)
+    reads, rows = [], []
+    for off in list(range(0, 40)) + [ref_len - 200, ref_len - 64 - k]:
+        for strand in (0, 1):
+            span = min(64 + k - 1 + off % 7, ref_len - off)
+            n = int(rng.integers(20, 90))
+            reads.append(rng.standard_normal(n).astype(np.float32))
+            rows.append((len(reads) - 1, off, span, strand, int(rng.integers(-1, 12)), 0, 0))
+    w = S._finish("kmers", pore, ref, ref_len, reads, rows, dict(k=k))
+    w.k = k
+    assert_bit_exact(run_gpu(w), run_oracle(w))
