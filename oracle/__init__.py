@@ -86,6 +86,13 @@ class Result(C.Structure):
     ]
 
 
+class Anchor(C.Structure):
+    _fields_ = [("q", C.c_uint32), ("t", C.c_uint32), ("len", C.c_uint32)]
+
+
+ANCHOR_DTYPE = np.dtype([("q", "<u4"), ("t", "<u4"), ("len", "<u4")])
+
+
 RESULT_DTYPE = np.dtype(
     {
         "names": [f[0] for f in Result._fields_],
@@ -133,6 +140,18 @@ def lib():
             L.ora_score_f32.argtypes = [f32, i64, f32]
             L.ora_score_f64.restype = f64
             L.ora_score_f64.argtypes = [f64, i64, f64]
+            pa = C.POINTER(Anchor)
+            L.ora_anchored_f32.restype = C.c_int
+            L.ora_anchored_f32.argtypes = [pf, i64, pf, i64, pa, i64, i64, pf, pu64]
+            L.ora_anchored_f64.restype = C.c_int
+            L.ora_anchored_f64.argtypes = [pd, i64, pd, i64, pa, i64, i64, pd, pu64]
+            L.ora_anchored_brute.restype = C.c_int
+            L.ora_anchored_brute.argtypes = [pd, i64, pd, i64, pa, i64, pd]
+            L.ora_map_anchored.restype = C.c_int
+            L.ora_map_anchored.argtypes = [
+                C.c_int, f32, f32, pf, pu8, u64, pf, pu64, C.c_uint32,
+                C.POINTER(Candidate), C.c_uint32, pa, pu64, C.POINTER(Result), C.c_int,
+            ]
             L.ora_map_batch.restype = C.c_int
             L.ora_map_batch.argtypes = [
                 C.c_int, f32, f32, C.c_int, pf, pu8, u64, pf, pu64, C.c_uint32,
@@ -284,6 +303,72 @@ def map_batch(k, b_match, score_threshold, end_mode, pore, ref2bit, ref_len, eve
         int(k), float(np.float32(b_match)), float(np.float32(score_threshold)), int(end_mode),
         _P(pore, C.c_float), _P(ref, C.c_uint8), int(ref_len), _P(ev, C.c_float), _P(offs, C.c_uint64),
         n_reads, cands.ctypes.data_as(C.POINTER(Candidate)), len(cands),
+        out.ctypes.data_as(C.POINTER(Result)), 1 if use_f64 else 0,
+    )
+    if rc != 0:
+        raise ValueError("oracle rejected the batch (%d)" % rc)
+    return out
+
+
+def _anchors(anchors):
+    a = np.ascontiguousarray(np.asarray(anchors, dtype=ANCHOR_DTYPE) if not isinstance(anchors, np.ndarray)
+                             or anchors.dtype != ANCHOR_DTYPE else anchors)
+    return a
+
+
+def anchored_f32(e, r, anchors, band_w=-1):
+    """Anchor-guided cost (Sec. 2.4.2), FP32: (cost, cells).  anchors: sequence
+    of (q, t, len) or an ANCHOR_DTYPE array."""
+    e, r, a = _f32(e), _f32(r), _anchors(anchors)
+    cost = C.c_float()
+    cells = C.c_uint64()
+    rc = lib().ora_anchored_f32(_P(e, C.c_float), len(e), _P(r, C.c_float), len(r),
+                                a.ctypes.data_as(C.POINTER(Anchor)), len(a), band_w, C.byref(cost), C.byref(cells))
+    if rc != 0:
+        raise ValueError("oracle rejected the anchors (%d)" % rc)
+    return np.float32(cost.value), cells.value
+
+
+def anchored_f64(e, r, anchors, band_w=-1):
+    e, r, a = _f64(e), _f64(r), _anchors(anchors)
+    cost = C.c_double()
+    cells = C.c_uint64()
+    rc = lib().ora_anchored_f64(_P(e, C.c_double), len(e), _P(r, C.c_double), len(r),
+                                a.ctypes.data_as(C.POINTER(Anchor)), len(a), band_w, C.byref(cost), C.byref(cells))
+    if rc != 0:
+        raise ValueError("oracle rejected the anchors (%d)" % rc)
+    return cost.value, cells.value
+
+
+def anchored_brute(e, r, anchors):
+    """Minimum path sum (FP64) over N/W/NW paths that stay in the gap rectangles,
+    one-sided gap lines and anchor diagonals; tiny tables only."""
+    e, r, a = _f64(e), _f64(r), _anchors(anchors)
+    cost = C.c_double()
+    rc = lib().ora_anchored_brute(_P(e, C.c_double), len(e), _P(r, C.c_double), len(r),
+                                  a.ctypes.data_as(C.POINTER(Anchor)), len(a), C.byref(cost))
+    if rc != 0:
+        raise ValueError("brute force is limited to tiny inputs with valid anchors")
+    return cost.value
+
+
+def map_anchored(k, b_match, score_threshold, pore, ref2bit, ref_len, events, read_offsets, cands, anchors,
+                 anchor_offsets, use_f64=False):
+    """Whole-path oracle for a batch in anchor-guided mode (GLOBAL ends)."""
+    pore = _f32(pore)
+    ref = np.ascontiguousarray(ref2bit, dtype=np.uint8)
+    ev = _f32(events)
+    offs = np.ascontiguousarray(read_offsets, dtype=np.uint64)
+    cands = np.ascontiguousarray(cands)
+    a = _anchors(anchors)
+    aoffs = np.ascontiguousarray(anchor_offsets, dtype=np.uint64)
+    assert len(aoffs) == len(cands) + 1
+    out = np.zeros(len(cands), RESULT_DTYPE)
+    rc = lib().ora_map_anchored(
+        int(k), float(np.float32(b_match)), float(np.float32(score_threshold)),
+        _P(pore, C.c_float), _P(ref, C.c_uint8), int(ref_len), _P(ev, C.c_float), _P(offs, C.c_uint64),
+        len(offs) - 1, cands.ctypes.data_as(C.POINTER(Candidate)), len(cands),
+        a.ctypes.data_as(C.POINTER(Anchor)), _P(aoffs, C.c_uint64),
         out.ctypes.data_as(C.POINTER(Result)), 1 if use_f64 else 0,
     )
     if rc != 0:

@@ -364,6 +364,9 @@ double ora_score_f64(double b_match, int64_t n_read, double cost)
  * work): non-finite event, empty read, segment outside the reference,
  * segment shorter than k, read index out of range, bad band slope.
  * ------------------------------------------------------------------------- */
+static void ora_decide(uint32_t n_reads, const ora_candidate_t *cands, uint32_t n_cands,
+                       float score_threshold, ora_result_t *out, int use_f64);
+
 int ora_map_batch(int k, float b_match, float score_threshold, int end_mode,
                   const float *pore, const uint8_t *ref2bit, uint64_t ref_len,
                   const float *events, const uint64_t *read_offsets,
@@ -446,7 +449,15 @@ int ora_map_batch(int k, float b_match, float score_threshold, int end_mode,
         free(r);
     }
 
-    /* per-read decision: scan candidates in index order, keep the first max */
+    ora_decide(n_reads, cands, n_cands, score_threshold, out, use_f64);
+    return 0;
+}
+
+/* Per-read decision (Sec. 2.3, Sec. 3.1): scan candidates in index order,
+ * keep the first maximum score; the read is mapped iff it is >= threshold. */
+static void ora_decide(uint32_t n_reads, const ora_candidate_t *cands, uint32_t n_cands,
+                       float score_threshold, ora_result_t *out, int use_f64)
+{
     int64_t *best = (int64_t *)malloc(sizeof(int64_t) * (n_reads ? n_reads : 1));
     for (uint32_t q = 0; q < n_reads; ++q)
         best[q] = -1;
@@ -468,5 +479,286 @@ int ora_map_batch(int k, float b_match, float score_threshold, int end_mode,
         out[c].decision = (bs >= (double)score_threshold) ? ORA_MAPPED : ORA_UNMAPPED;
     }
     free(best);
+}
+
+/* ---------------------------------------------------------------------------
+ * Anchor-guided alignment (Sec. 2.4.2).  A chain gives K anchors, each a run
+ * of L events e[q..q+L-1] matched one to one to expected values r[t..t+L-1]
+ * (the anchor's diagonal), sorted and disjoint in both sequences.  Only the
+ * gaps between anchors are aligned by DTW; the anchors' own cells lie on the
+ * diagonal.  Reading taken where the paper leaves details open:
+ *   - the alignment runs from (0,0) to (n-1,m-1) and visits, in order,
+ *     gap 0, anchor 1, gap 1, ..., anchor K, gap K;
+ *   - gap k covers rows [end of anchor k, start of anchor k+1) and the same
+ *     for columns (anchor 0 ends at (0,0), anchor K+1 starts at (n,m));
+ *   - a gap with rows and columns is a global DTW of its own (anchored start
+ *     at its first cell, corner end), banded around the line through its own
+ *     corners with the candidate's half-width;
+ *   - a gap with rows but no columns aligns each of its events to one
+ *     expected value: the previous anchor's last value (the first anchor's
+ *     first value for gap 0); symmetrically for columns without rows;
+ *   - an anchor adds |e - r| of its diagonal cells, summed in order;
+ *   - C = the pieces' costs added in path order, starting from the first
+ *     piece; N_Read = n (every event is on the path).
+ * Each piece's cost is a sum accumulated from its own first cell, so C is
+ * the minimum path cost over paths that stay inside the gap rectangles and
+ * anchor diagonals, evaluated piece by piece.
+ * ------------------------------------------------------------------------- */
+static int ora_anchors_valid(int64_t n, int64_t m, const ora_anchor_t *A, int64_t K)
+{
+    int64_t pq = 0, pt = 0;
+    for (int64_t a = 0; a < K; ++a) {
+        if (A[a].len < 1)
+            return 0;
+        if ((int64_t)A[a].q < pq || (int64_t)A[a].t < pt)
+            return 0;
+        pq = (int64_t)A[a].q + A[a].len;
+        pt = (int64_t)A[a].t + A[a].len;
+        if (pq > n || pt > m)
+            return 0;
+    }
+    return 1;
+}
+
+#define ORA_ANCHORED_BODY(T, ABS, DTW)                                          \
+    if (!ora_anchors_valid(n, m, A, K))                                         \
+        return -1;                                                              \
+    T C = 0;                                                                    \
+    int first = 1;                                                              \
+    uint64_t cl = 0;                                                            \
+    int64_t pq = 0, pt = 0;                                                     \
+    for (int64_t a = 0; a <= K; ++a) {                                          \
+        const int64_t q1 = (a < K) ? (int64_t)A[a].q : n;                       \
+        const int64_t t1 = (a < K) ? (int64_t)A[a].t : m;                       \
+        const int64_t nr = q1 - pq, nc = t1 - pt;                               \
+        int has = 0;                                                            \
+        T piece = 0;                                                            \
+        if (nr > 0 && nc > 0) {                                                 \
+            T g;                                                                \
+            int64_t ei, ej, we;                                                 \
+            uint64_t gc;                                                        \
+            if (DTW(e + pq, nr, r + pt, nc, band_w, 0, 0, ORA_END_GLOBAL, &g,   \
+                    &ei, &ej, &gc, &we, NULL) != 0)                             \
+                return -1;                                                      \
+            piece = g;                                                          \
+            cl += gc;                                                           \
+            has = 1;                                                            \
+        } else if (nr > 0) {                                                    \
+            const int64_t col = (a > 0) ? pt - 1 : t1;                          \
+            T s = 0;                                                            \
+            for (int64_t i = pq; i < q1; ++i) {                                 \
+                T diff = e[i] - r[col];                                         \
+                T dd = ABS(diff);                                               \
+                s = (i == pq) ? dd : s + dd;                                    \
+            }                                                                   \
+            piece = s;                                                          \
+            cl += (uint64_t)nr;                                                 \
+            has = 1;                                                            \
+        } else if (nc > 0) {                                                    \
+            const int64_t row = (a > 0) ? pq - 1 : q1;                          \
+            T s = 0;                                                            \
+            for (int64_t j = pt; j < t1; ++j) {                                 \
+                T diff = e[row] - r[j];                                         \
+                T dd = ABS(diff);                                               \
+                s = (j == pt) ? dd : s + dd;                                    \
+            }                                                                   \
+            piece = s;                                                          \
+            cl += (uint64_t)nc;                                                 \
+            has = 1;                                                            \
+        }                                                                       \
+        if (has) {                                                              \
+            C = first ? piece : C + piece;                                      \
+            first = 0;                                                          \
+        }                                                                       \
+        if (a < K) {                                                            \
+            T s = 0;                                                            \
+            for (int64_t x = 0; x < (int64_t)A[a].len; ++x) {                   \
+                T diff = e[A[a].q + x] - r[A[a].t + x];                         \
+                T dd = ABS(diff);                                               \
+                s = (x == 0) ? dd : s + dd;                                     \
+            }                                                                   \
+            C = first ? s : C + s;                                              \
+            first = 0;                                                          \
+            cl += A[a].len;                                                     \
+            pq = (int64_t)A[a].q + A[a].len;                                    \
+            pt = (int64_t)A[a].t + A[a].len;                                    \
+        }                                                                       \
+    }                                                                           \
+    *cost = C;                                                                  \
+    *cells = cl;                                                                \
+    return 0;
+
+int ora_anchored_f32(const float *e, int64_t n, const float *r, int64_t m,
+                     const ora_anchor_t *A, int64_t K, int64_t band_w,
+                     float *cost, uint64_t *cells)
+{
+    ORA_ANCHORED_BODY(float, fabsf, ora_dtw_f32)
+}
+
+int ora_anchored_f64(const double *e, int64_t n, const double *r, int64_t m,
+                     const ora_anchor_t *A, int64_t K, int64_t band_w,
+                     double *cost, uint64_t *cells)
+{
+    ORA_ANCHORED_BODY(double, fabs, ora_dtw_f64)
+}
+
+/* Brute force for the anchored reading: every N / W / NW path from (0,0) to
+ * (n-1,m-1) that visits every anchor cell and whose cells all lie in a gap
+ * rectangle, on a one-sided gap's line, or on an anchor's diagonal; the
+ * minimum path sum (FP64, tiny tables). */
+typedef struct {
+    const double *e, *r;
+    int64_t n, m;
+    const uint8_t *ok;  /* 1: gap cell, 2: anchor cell */
+    int64_t n_anchor_cells;
+    double best;
+} ora_abf_t;
+
+static void abf_walk(ora_abf_t *s, int64_t i, int64_t j, double acc, int64_t seen)
+{
+    if (i == s->n - 1 && j == s->m - 1) {
+        if (seen == s->n_anchor_cells && acc < s->best)
+            s->best = acc;
+        return;
+    }
+    static const int di[3] = {0, 1, 1}, dj[3] = {1, 0, 1};
+    for (int mv = 0; mv < 3; ++mv) {
+        int64_t ni = i + di[mv], nj = j + dj[mv];
+        if (ni >= s->n || nj >= s->m || !s->ok[ni * s->m + nj])
+            continue;
+        abf_walk(s, ni, nj, acc + fabs(s->e[ni] - s->r[nj]), seen + (s->ok[ni * s->m + nj] == 2));
+    }
+}
+
+int ora_anchored_brute(const double *e, int64_t n, const double *r, int64_t m,
+                       const ora_anchor_t *A, int64_t K, double *cost)
+{
+    if (n < 1 || m < 1 || n > 9 || m > 9 || !ora_anchors_valid(n, m, A, K))
+        return -1;
+    uint8_t ok[81];
+    memset(ok, 0, sizeof ok);
+    int64_t pq = 0, pt = 0;
+    for (int64_t a = 0; a <= K; ++a) {
+        const int64_t q1 = (a < K) ? (int64_t)A[a].q : n;
+        const int64_t t1 = (a < K) ? (int64_t)A[a].t : m;
+        if (q1 > pq && t1 > pt) {
+            for (int64_t i = pq; i < q1; ++i)
+                for (int64_t j = pt; j < t1; ++j)
+                    ok[i * m + j] = 1;
+        } else if (q1 > pq) {
+            const int64_t col = (a > 0) ? pt - 1 : t1;
+            for (int64_t i = pq; i < q1; ++i)
+                ok[i * m + col] = 1;
+        } else if (t1 > pt) {
+            const int64_t row = (a > 0) ? pq - 1 : q1;
+            for (int64_t j = pt; j < t1; ++j)
+                ok[row * m + j] = 1;
+        }
+        if (a < K) {
+            for (int64_t x = 0; x < (int64_t)A[a].len; ++x)
+                ok[(A[a].q + x) * m + A[a].t + x] = 2;
+            pq = (int64_t)A[a].q + A[a].len;
+            pt = (int64_t)A[a].t + A[a].len;
+        }
+    }
+    int64_t n_anchor_cells = 0;
+    for (int64_t a = 0; a < K; ++a)
+        n_anchor_cells += A[a].len;
+    ora_abf_t s = {e, r, n, m, ok, n_anchor_cells, (double)INFINITY};
+    if (ok[0])
+        abf_walk(&s, 0, 0, fabs(e[0] - r[0]), ok[0] == 2);
+    *cost = s.best;
+    return 0;
+}
+
+/* Whole-path oracle for a batch in anchor-guided mode: as ora_map_batch with
+ * GLOBAL ends, each candidate c aligned through its anchors
+ * anchors[anchor_offsets[c] .. anchor_offsets[c+1]) (columns relative to the
+ * candidate's expected-signal row).  end = (n-1, m-1); w_eff reports the
+ * given half-width (-1 without a band); cells = DP cells of the gaps plus the
+ * cells on anchors and one-sided gaps. */
+int ora_map_anchored(int k, float b_match, float score_threshold,
+                     const float *pore, const uint8_t *ref2bit, uint64_t ref_len,
+                     const float *events, const uint64_t *read_offsets,
+                     uint32_t n_reads, const ora_candidate_t *cands,
+                     uint32_t n_cands, const ora_anchor_t *anchors,
+                     const uint64_t *anchor_offsets, ora_result_t *out, int use_f64)
+{
+    if (k < 1 || k > 12)
+        return -1;
+    for (uint32_t q = 0; q < n_reads; ++q) {
+        if (read_offsets[q + 1] <= read_offsets[q])
+            return -1;
+        for (uint64_t x = read_offsets[q]; x < read_offsets[q + 1]; ++x)
+            if (!isfinite(events[x]))
+                return -1;
+    }
+    for (uint32_t c = 0; c < n_cands; ++c) {
+        const ora_candidate_t *cd = &cands[c];
+        if (cd->read_id >= n_reads || cd->strand > 1)
+            return -1;
+        if (cd->ref_offset > ref_len || cd->ref_len_bases > ref_len - cd->ref_offset)
+            return -1;
+        if ((int64_t)cd->ref_len_bases < k)
+            return -1;
+        if (anchor_offsets[c + 1] < anchor_offsets[c])
+            return -1;
+        int64_t n = (int64_t)(read_offsets[cd->read_id + 1] - read_offsets[cd->read_id]);
+        int64_t m = (int64_t)cd->ref_len_bases - k + 1;
+        if (!ora_anchors_valid(n, m, anchors + anchor_offsets[c],
+                               (int64_t)(anchor_offsets[c + 1] - anchor_offsets[c])))
+            return -1;
+    }
+    for (uint32_t c = 0; c < n_cands; ++c) {
+        const ora_candidate_t *cd = &cands[c];
+        int64_t n = (int64_t)(read_offsets[cd->read_id + 1] - read_offsets[cd->read_id]);
+        const float *e = events + read_offsets[cd->read_id];
+        int64_t m = (int64_t)cd->ref_len_bases - k + 1;
+        uint8_t *codes = (uint8_t *)malloc(cd->ref_len_bases);
+        float *r = (float *)malloc(sizeof(float) * (size_t)m);
+        ora_segment_codes(ref2bit, ref_len, cd->ref_offset, cd->ref_len_bases, cd->strand, codes);
+        ora_expected_signal(codes, cd->ref_len_bases, k, pore, r);
+        const ora_anchor_t *A = anchors + anchor_offsets[c];
+        int64_t K = (int64_t)(anchor_offsets[c + 1] - anchor_offsets[c]);
+        ora_result_t *o = &out[c];
+        memset(o, 0, sizeof *o);
+        o->read_id = cd->read_id;
+        o->cand_idx = c;
+        uint64_t cells = 0;
+        int rc;
+        if (!use_f64) {
+            float cost;
+            rc = ora_anchored_f32(e, n, r, m, A, K, cd->band_w, &cost, &cells);
+            o->cost = cost;
+            o->score = ora_score_f32(b_match, n, cost);
+            o->cost64 = cost;
+            o->score64 = o->score;
+        } else {
+            double *e64 = (double *)malloc(sizeof(double) * (size_t)n);
+            double *r64 = (double *)malloc(sizeof(double) * (size_t)m);
+            for (int64_t x = 0; x < n; ++x)
+                e64[x] = e[x];
+            for (int64_t x = 0; x < m; ++x)
+                r64[x] = r[x];
+            double cost;
+            rc = ora_anchored_f64(e64, n, r64, m, A, K, cd->band_w, &cost, &cells);
+            o->cost64 = cost;
+            o->score64 = ora_score_f64((double)b_match, n, cost);
+            o->cost = (float)cost;
+            o->score = (float)o->score64;
+            free(e64);
+            free(r64);
+        }
+        free(codes);
+        free(r);
+        if (rc != 0)
+            return -1;
+        o->end_i = (int32_t)(n - 1);
+        o->end_j = (int32_t)(m - 1);
+        o->cells = cells;
+        o->w_eff = cd->band_w < 0 ? -1 : cd->band_w;
+        o->status = 0;
+    }
+    ora_decide(n_reads, cands, n_cands, score_threshold, out, use_f64);
     return 0;
 }

@@ -76,6 +76,26 @@ int ora_brute_f64(const double *e, int64_t n, const double *r, int64_t m,
                   double *cost, int64_t *end_j, uint64_t *paths);
 float ora_score_f32(float b_match, int64_t n_read, float cost);
 double ora_score_f64(double b_match, int64_t n_read, double cost);
+/* One anchor of a chain (Sec. 2.4.2): events q..q+len-1 on the diagonal
+ * with expected values t..t+len-1 of the candidate's region. */
+typedef struct {
+    uint32_t q, t, len;
+} ora_anchor_t;
+
+int ora_anchored_f32(const float *e, int64_t n, const float *r, int64_t m,
+                     const ora_anchor_t *A, int64_t K, int64_t band_w,
+                     float *cost, uint64_t *cells);
+int ora_anchored_f64(const double *e, int64_t n, const double *r, int64_t m,
+                     const ora_anchor_t *A, int64_t K, int64_t band_w,
+                     double *cost, uint64_t *cells);
+int ora_anchored_brute(const double *e, int64_t n, const double *r, int64_t m,
+                       const ora_anchor_t *A, int64_t K, double *cost);
+int ora_map_anchored(int k, float b_match, float score_threshold,
+                     const float *pore, const uint8_t *ref2bit, uint64_t ref_len,
+                     const float *events, const uint64_t *read_offsets,
+                     uint32_t n_reads, const ora_candidate_t *cands,
+                     uint32_t n_cands, const ora_anchor_t *anchors,
+                     const uint64_t *anchor_offsets, ora_result_t *out, int use_f64);
 int ora_map_batch(int k, float b_match, float score_threshold, int end_mode,
                   const float *pore, const uint8_t *ref2bit, uint64_t ref_len,
                   const float *events, const uint64_t *read_offsets,

@@ -299,3 +299,139 @@ def test_planted_mistakes_are_caught():
         if dtw_no_nw(e, r) != O.brute_f32(e, r)[0]:
             diffs += 1
     assert diffs > 50
+
+
+# ---------------------------------------------------------------- anchor-guided alignment (Sec. 2.4.2)
+def _load_anchored():
+    rows = []
+    for line in open(os.path.join(GOLD, "anchored_hand_worked.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, ev, rv, an, bw, cost, cells = [x.strip() for x in line.split("|")]
+        anchors = [tuple(int(v) for v in a.split(",")) for a in an.split(";") if a]
+        rows.append((name, [float(x) for x in ev.split()], [float(x) for x in rv.split()], anchors, int(bw),
+                     float(cost), int(cells)))
+    return rows
+
+
+@pytest.mark.parametrize("case", _load_anchored(), ids=lambda c: c[0])
+def test_anchored_hand_worked(case):
+    name, e, r, anchors, bw, cost, cells = case
+    c32, n32 = O.anchored_f32(e, r, anchors, bw)
+    c64, n64 = O.anchored_f64(e, r, anchors, bw)
+    assert float(c32) == cost and c64 == cost
+    assert n32 == cells == n64
+    assert O.anchored_brute(e, r, anchors) == cost
+
+
+def _random_anchors(rng, n, m, max_k=3):
+    """Sorted, disjoint anchors inside an n x m table (may be empty)."""
+    anchors = []
+    q, t = 0, 0
+    for _ in range(int(rng.integers(0, max_k + 1))):
+        if q >= n or t >= m:
+            break
+        q0 = int(rng.integers(q, n))
+        t0 = int(rng.integers(t, m))
+        ln = int(rng.integers(1, min(n - q0, m - t0) + 1))
+        anchors.append((q0, t0, ln))
+        q, t = q0 + ln, t0 + ln
+    return anchors
+
+
+def test_anchored_equals_brute_force_on_integer_tables():
+    """The piecewise evaluation equals the minimum over all paths that stay in
+    the gap rectangles, one-sided gap lines and anchor diagonals (integer
+    values: every sum is exact, so equality is bit for bit)."""
+    rng = np.random.default_rng(2024)
+    checked = 0
+    for _ in range(2500):
+        n, m = int(rng.integers(1, 8)), int(rng.integers(1, 8))
+        e = rng.integers(-4, 5, size=n).astype(np.float64)
+        r = rng.integers(-4, 5, size=m).astype(np.float64)
+        anchors = _random_anchors(rng, n, m)
+        bf = O.anchored_brute(e, r, anchors)
+        c64, _ = O.anchored_f64(e, r, anchors)
+        c32, _ = O.anchored_f32(e, r, anchors)
+        assert c64 == bf and float(c32) == bf, (e, r, anchors, bf, c64, c32)
+        checked += len(anchors) > 0
+    assert checked > 1500
+
+
+def test_anchored_without_anchors_is_plain_dtw_and_never_below_it():
+    rng = np.random.default_rng(7)
+    for _ in range(400):
+        n, m = int(rng.integers(1, 12)), int(rng.integers(1, 12))
+        e = rng.integers(-5, 6, size=n).astype(np.float32)
+        r = rng.integers(-5, 6, size=m).astype(np.float32)
+        bw = int(rng.integers(-1, 4))
+        plain = O.dtw_f32(e, r, bw)[0]
+        assert O.anchored_f32(e, r, [], bw)[0] == plain
+        # with anchors (unbanded), the cost can only grow: fewer paths
+        anchors = _random_anchors(rng, n, m)
+        assert O.anchored_f32(e, r, anchors)[0] >= O.dtw_f32(e, r)[0]
+
+
+def test_anchored_full_diagonal_closed_form():
+    """One anchor over the whole diagonal of an n x n table: the cost is the
+    sequential FP32 sum of |e_i - r_i|."""
+    rng = np.random.default_rng(9)
+    for n in (1, 2, 5, 33, 200):
+        e = rng.standard_normal(n).astype(np.float32)
+        r = rng.standard_normal(n).astype(np.float32)
+        s = np.float32(0)
+        for i in range(n):
+            d = np.float32(abs(np.float32(e[i] - r[i])))
+            s = d if i == 0 else np.float32(s + d)
+        c, cells = O.anchored_f32(e, r, [(0, 0, n)])
+        assert c == s and cells == n
+
+
+def test_anchored_rejects_bad_chains():
+    e = np.zeros(6, np.float32)
+    r = np.zeros(6, np.float32)
+    for bad in ([(0, 0, 0)], [(2, 2, 2), (3, 5, 1)], [(2, 2, 2), (5, 3, 1)], [(4, 4, 3)], [(0, 5, 2)]):
+        with pytest.raises(ValueError):
+            O.anchored_f32(e, r, bad)
+
+
+def test_planted_anchor_mistake_is_caught():
+    """A variant that aligns a one-sided gap to the next anchor's first value
+    instead of the previous anchor's last one disagrees with the brute force."""
+    def wrong(e, r, anchors):
+        C, pq, pt, first = 0.0, 0, 0, True
+        n, m = len(e), len(r)
+        for a in range(len(anchors) + 1):
+            q1, t1 = (anchors[a][0], anchors[a][1]) if a < len(anchors) else (n, m)
+            nr, nc = q1 - pq, t1 - pt
+            piece = None
+            if nr > 0 and nc > 0:
+                piece = O.dtw_f64(e[pq:q1], r[pt:t1])[0]
+            elif nr > 0:
+                col = min(t1, m - 1)  # the planted mistake
+                piece = sum(abs(e[i] - r[col]) for i in range(pq, q1))
+            elif nc > 0:
+                row = pq - 1 if a > 0 else q1
+                piece = sum(abs(e[row] - r[j]) for j in range(pt, t1))
+            if piece is not None:
+                C = piece if first else C + piece
+                first = False
+            if a < len(anchors):
+                q, t, ln = anchors[a]
+                s = sum(abs(e[q + x] - r[t + x]) for x in range(ln))
+                C = s if first else C + s
+                first = False
+                pq, pt = q + ln, t + ln
+        return C
+
+    rng = np.random.default_rng(5)
+    diffs = 0
+    for _ in range(1500):
+        n, m = int(rng.integers(2, 8)), int(rng.integers(2, 8))
+        e = rng.integers(-4, 5, size=n).astype(np.float64)
+        r = rng.integers(-4, 5, size=m).astype(np.float64)
+        anchors = _random_anchors(rng, n, m)
+        if wrong(e, r, anchors) != O.anchored_brute(e, r, anchors):
+            diffs += 1
+    assert diffs > 20
