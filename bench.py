@@ -42,6 +42,9 @@ WORKLOADS = {
                   "FP32 global DTW"),
     "longread": ("longread_banded: 2000 reads of 20k-100k events (uniform), 2 candidates each on a 100 Mb "
                  "reference, band 5% of span, 5% skips + 5% stays, noise sd 0.4, FP32 global DTW"),
+    "anchored": ("anchored_batched: the batched-uneven shapes (20000 reads, 1-8 candidates, band 10% of span) "
+                 "with anchor-guided alignment: each candidate's chain (true locus: runs of one event per k-mer "
+                 "from the simulated read, 8-16 events; decoys: 0-6 random anchors), gaps aligned by banded DTW"),
     "plain": ("plain: 64 reads x 500 events, 1 candidate each (true 550-value segment of a 20 kb reference), "
               "unbanded FP32 DTW"),
 }
@@ -167,8 +170,12 @@ def cpu_baseline(w, seconds=15.0, seed=1):
     while time.perf_counter() - t0 < seconds and pos < len(order):
         sub = w.subset(np.sort(order[pos : pos + chunk]))
         pos += chunk
-        res = O.map_batch(sub.k, sub.b_match, sub.score_threshold, sub.end_mode, sub.pore, sub.ref2bit,
-                          sub.ref_len, sub.events, sub.read_offsets, sub.cands)
+        if sub.anchor_offsets is not None:
+            res = O.map_anchored(sub.k, sub.b_match, sub.score_threshold, sub.pore, sub.ref2bit, sub.ref_len,
+                                 sub.events, sub.read_offsets, sub.cands, sub.anchors, sub.anchor_offsets)
+        else:
+            res = O.map_batch(sub.k, sub.b_match, sub.score_threshold, sub.end_mode, sub.pore, sub.ref2bit,
+                              sub.ref_len, sub.events, sub.read_offsets, sub.cands)
         cells += int(res["cells"].sum())
         done += len(res)
     el = time.perf_counter() - t0
@@ -225,9 +232,15 @@ def main():
     m_total = int(np.sum(w.cands["ref_len_bases"].astype(np.int64) - w.k + 1))
     need = B.rawalign_dtw_batch_bytes(len(w.events), w.n_reads, w.n_cands, m_total)
     arena = 2 * need + len(w.ref2bit) + (256 << 20)
+    if w.anchor_offsets is not None:  # per-gap work items and results, pieces
+        arena += 2 * (len(w.anchors) + w.n_cands) * 512
     al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena, device="cuda:%d" % local)
     stream = al.stream
-    batch = al.prepare(w.events, w.read_offsets, w.cands)
+    anchored = w.anchor_offsets is not None
+    if anchored:
+        batch = al.prepare_anchored(w.events, w.read_offsets, w.cands, w.anchors, w.anchor_offsets)
+    else:
+        batch = al.prepare(w.events, w.read_offsets, w.cands)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:%d" % local)
 
     def one_step():
@@ -310,7 +323,10 @@ def main():
         sub = w.subset(np.sort(perm[:keep]))
         alp = B.Aligner(sub.pore, sub.ref2bit, sub.ref_len, arena_bytes=1 << 30, kernel=B.RA_KERNEL_PLAIN,
                         device="cuda:%d" % local)
-        bp = alp.prepare(sub.events, sub.read_offsets, sub.cands)
+        if anchored:
+            bp = alp.prepare_anchored(sub.events, sub.read_offsets, sub.cands, sub.anchors, sub.anchor_offsets)
+        else:
+            bp = alp.prepare(sub.events, sub.read_offsets, sub.cands)
         tp = alp.run(bp)
         rp = alp.poll(tp, sub.n_cands)
         tp = alp.run(bp)
@@ -332,16 +348,20 @@ def main():
         off_np = off_h.numpy().view(np.uint64)
         cand_np = cand_h.numpy().view(S.CANDIDATE_DTYPE)
         for _ in range(2):
-            r = al.align(ev_np, off_np, cand_np)
+            r = (al.align_anchored(ev_np, off_np, cand_np, w.anchors, w.anchor_offsets) if anchored
+                 else al.align(ev_np, off_np, cand_np))
         barrier(world)
         t0 = time.perf_counter()
         e2e_steps = max(3, args.steps // 2)
         for _ in range(e2e_steps):
-            r = al.align(ev_np, off_np, cand_np)
+            r = (al.align_anchored(ev_np, off_np, cand_np, w.anchors, w.anchor_offsets) if anchored
+                 else al.align(ev_np, off_np, cand_np))
         el = max_over_ranks(time.perf_counter() - t0, world)
         e2e_cells = sum_over_ranks(float(r["cells"].sum()) * e2e_steps, world)
         out["e2e"] = {"value": round(e2e_cells / el / 1e9, 2), "unit": "GCUPS",
-                      "h2d_bytes_per_step": int(w.events.nbytes + w.read_offsets.nbytes + w.cands.nbytes),
+                      "h2d_bytes_per_step": int(w.events.nbytes + w.read_offsets.nbytes + w.cands.nbytes +
+                                                (w.anchors.nbytes + w.anchor_offsets.nbytes
+                                                 if w.anchor_offsets is not None else 0)),
                       "d2h_bytes_per_step": int(w.n_cands * B.RESULT_DTYPE.itemsize),
                       "ms_per_step": round(el / e2e_steps * 1e3, 2)}
 

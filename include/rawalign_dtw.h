@@ -93,6 +93,15 @@ typedef struct {
     int64_t slope_den;         /* 0,0 = (m-1)/(n-1), the paper's length ratio  */
 } rawalign_candidate_t;
 
+/* One anchor of a chain (Sec. 2.4.2), 12 bytes: read events q .. q+len-1
+ * matched one to one, on the diagonal, to the expected values t .. t+len-1
+ * of the candidate's region (columns counted from the region's first k-mer). */
+typedef struct {
+    uint32_t q;
+    uint32_t t;
+    uint32_t len;
+} rawalign_anchor_t;
+
 /* Result of one candidate (56 bytes). */
 typedef struct {
     uint64_t read_id;
@@ -215,6 +224,41 @@ int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_events, const f
  * of "G HR cost" lines with the same numbers.  Returns RA_EINVAL for a wrong
  * count or a non-positive cost. */
 int rawalign_dtw_set_variant_costs(rawalign_dtw_t *h, const double *costs, uint32_t n);
+
+/* Anchor-guided batch (Sec. 2.4.2): as rawalign_dtw_prepare_batch, but each
+ * candidate c is aligned through its chain anchors[anchor_offsets[c] ..
+ * anchor_offsets[c+1]) (host arrays, copied before return; anchor_offsets
+ * has n_cands+1 entries; anchors may be NULL when every chain is empty).
+ * Only the gaps between anchors are aligned:
+ *   - the path runs from (0,0) to (n-1,m-1) through gap 0, anchor 1, gap 1,
+ *     ..., anchor K, gap K; gap k spans the rows and columns between the end
+ *     of anchor k and the start of anchor k+1;
+ *   - a gap with rows and columns is a global DTW of its own, banded around
+ *     the line through its corners with the candidate's half-width band_w
+ *     (< 0: no band; the candidate's slope is not used);
+ *   - a gap with rows only aligns its events to the previous anchor's last
+ *     value (the first anchor's first value for gap 0), a gap with columns
+ *     only its values to the previous anchor's last event (the first
+ *     anchor's first event); an anchor adds |e - r| along its diagonal;
+ *   - C = the pieces' costs added in path order, N_Read = n, end = (n-1,m-1),
+ *     w_eff = band_w (-1 without a band), cells = DP cells of the gaps plus
+ *     the cells of anchors and one-sided gaps.  The end is GLOBAL whatever
+ *     the handle's end_mode.
+ * The arena needs, beyond rawalign_dtw_batch_bytes, about 200 bytes per gap
+ * and 32 per anchor.  Errors: as rawalign_dtw_prepare_batch, and RA_EINVAL
+ * for a chain that is unsorted, overlapping, of zero length or outside the
+ * n x m table. */
+int rawalign_dtw_prepare_anchored(rawalign_dtw_t *h, const float *events, const uint64_t *read_offsets,
+                                  uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
+                                  const rawalign_anchor_t *anchors, const uint64_t *anchor_offsets,
+                                  uint64_t *batch);
+
+/* Prepares, runs and releases an anchor-guided batch in one call (see
+ * rawalign_dtw_prepare_anchored); the results come from rawalign_dtw_poll. */
+int rawalign_dtw_submit_anchored(rawalign_dtw_t *h, const float *events, const uint64_t *read_offsets,
+                                 uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
+                                 const rawalign_anchor_t *anchors, const uint64_t *anchor_offsets,
+                                 uint64_t *ticket);
 
 /* Bytes of arena a batch of this shape needs (planning aid for callers).
  * Not included: ring scratch for alignments whose band is too wide for the

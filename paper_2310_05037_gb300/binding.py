@@ -12,7 +12,7 @@ import os
 
 import numpy as np
 
-from .synth import CANDIDATE_DTYPE
+from .synth import ANCHOR_DTYPE, CANDIDATE_DTYPE
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librawalign_dtw.so")
@@ -112,6 +112,10 @@ SIGNATURES = {
     "rawalign_dtw_flush": (C.c_int, [C.c_void_p]),
     "rawalign_dtw_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.c_int64]),
     "rawalign_dtw_prepare_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, _u64p]),
+    "rawalign_dtw_prepare_anchored": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
+                                                C.c_uint32, C.c_void_p, C.c_void_p, _u64p]),
+    "rawalign_dtw_submit_anchored": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
+                                               C.c_uint32, C.c_void_p, C.c_void_p, _u64p]),
     "rawalign_dtw_run_batch": (C.c_int, [C.c_void_p, C.c_uint64, _u64p]),
     "rawalign_dtw_release_batch": (C.c_int, [C.c_void_p, C.c_uint64]),
     "rawalign_dtw_destroy": (C.c_int, [C.c_void_p]),
@@ -183,6 +187,36 @@ def rawalign_dtw_prepare_batch(h, events, read_offsets, cands) -> int:
     _check("rawalign_dtw_prepare_batch", load().rawalign_dtw_prepare_batch(
         h, _ptr(ev), _ptr(offs), len(offs) - 1, _ptr(cands), len(cands), C.byref(b)))
     return b.value
+
+
+def _anchor_args(anchors, anchor_offsets, n_cands):
+    aoffs = np.ascontiguousarray(anchor_offsets, np.uint64)
+    if len(aoffs) != n_cands + 1:
+        raise ValueError("anchor_offsets needs n_cands + 1 entries")
+    a = np.ascontiguousarray(anchors if anchors is not None else np.zeros(0, ANCHOR_DTYPE))
+    if a.dtype != ANCHOR_DTYPE:
+        a = np.ascontiguousarray(np.asarray(a, dtype=ANCHOR_DTYPE))
+    return a, aoffs
+
+
+def rawalign_dtw_prepare_anchored(h, events, read_offsets, cands, anchors, anchor_offsets) -> int:
+    ev, offs, cands = _batch_args(events, read_offsets, cands)
+    a, aoffs = _anchor_args(anchors, anchor_offsets, len(cands))
+    b = C.c_uint64()
+    _check("rawalign_dtw_prepare_anchored", load().rawalign_dtw_prepare_anchored(
+        h, _ptr(ev), _ptr(offs), len(offs) - 1, _ptr(cands), len(cands), _ptr(a) if len(a) else None, _ptr(aoffs),
+        C.byref(b)))
+    return b.value
+
+
+def rawalign_dtw_submit_anchored(h, events, read_offsets, cands, anchors, anchor_offsets) -> int:
+    ev, offs, cands = _batch_args(events, read_offsets, cands)
+    a, aoffs = _anchor_args(anchors, anchor_offsets, len(cands))
+    t = C.c_uint64()
+    _check("rawalign_dtw_submit_anchored", load().rawalign_dtw_submit_anchored(
+        h, _ptr(ev), _ptr(offs), len(offs) - 1, _ptr(cands), len(cands), _ptr(a) if len(a) else None, _ptr(aoffs),
+        C.byref(t)))
+    return t.value
 
 
 def rawalign_dtw_run_batch(h, batch: int) -> int:
@@ -292,6 +326,13 @@ class Aligner:
 
     def prepare(self, events, read_offsets, cands):
         return rawalign_dtw_prepare_batch(self.h, events, read_offsets, cands)
+
+    def align_anchored(self, events, read_offsets, cands, anchors, anchor_offsets, timeout_us=-1):
+        t = rawalign_dtw_submit_anchored(self.h, events, read_offsets, cands, anchors, anchor_offsets)
+        return rawalign_dtw_poll(self.h, t, len(cands), timeout_us)
+
+    def prepare_anchored(self, events, read_offsets, cands, anchors, anchor_offsets):
+        return rawalign_dtw_prepare_anchored(self.h, events, read_offsets, cands, anchors, anchor_offsets)
 
     def run(self, batch):
         return rawalign_dtw_run_batch(self.h, batch)

@@ -5,6 +5,7 @@
 //   (dtw_stripe_kernel, the hot loop, is in stripe_kernel.cu)
 //   dtw_plain_kernel         the same alignment by one CTA per launch, one
 //                            anti-diagonal per __syncthreads (reference point)
+//   combine_kernel           Sec. 2.4.2: anchor-guided cost from its pieces
 //   decide_kernel            Sec. 2.3 / 3.1: best candidate per read, threshold
 //
 // Arithmetic follows the definitions in a fixed order: d = |e - r| (one
@@ -191,6 +192,55 @@ __global__ void __launch_bounds__(256) dtw_plain_kernel(const WorkDesc *__restri
 }
 
 // ---------------------------------------------------------------------------
+// Anchor-guided alignment (Sec. 2.4.2): a candidate's cost is its pieces'
+// costs added in path order, starting from the first piece; a run of cells
+// (an anchor's diagonal, or a gap with rows or columns only) is summed from
+// its first cell.  One thread per candidate keeps the order fixed; then the
+// score (Sec. 2.3) and the per-read best key as in the DTW kernels.
+// ---------------------------------------------------------------------------
+__global__ void combine_kernel(const CombineDesc *__restrict__ desc, int n, const PieceRef *__restrict__ plan,
+                               const rawalign_result_t *__restrict__ pieces, const float *__restrict__ events,
+                               const float *__restrict__ r_all, rawalign_result_t *__restrict__ results,
+                               unsigned long long *best_keys, float b_match)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const CombineDesc cd = desc[c];
+        float C = 0.f;
+        unsigned long long cells = 0;
+        for (uint32_t p = 0; p < cd.count; ++p) {
+            const PieceRef pr = plan[cd.first + p];
+            float piece;
+            if (pr.kind == 0) {
+                piece = pieces[pr.idx].cost;
+                cells += pieces[pr.idx].cells;
+            } else {
+                const float *e = events + pr.ev;
+                const float *r = r_all + pr.r;
+                piece = 0.f;
+                for (uint32_t x = 0; x < pr.len; ++x) {
+                    const float d = fabsf(__fsub_rn(e[x * pr.ev_step], r[x * pr.r_step]));
+                    piece = (x == 0) ? d : __fadd_rn(piece, d);
+                }
+                cells += pr.len;
+            }
+            C = (p == 0) ? piece : __fadd_rn(C, piece);
+        }
+        const float sc = __fsub_rn(__fmul_rn(b_match, (float)cd.n), C);
+        rawalign_result_t *o = results + c;
+        o->read_id = (uint64_t)cd.read;
+        o->cand_idx = (uint32_t)c;
+        o->cost = C;
+        o->score = sc;
+        o->end_i = cd.n - 1;
+        o->end_j = cd.m - 1;
+        o->w_eff = cd.w_report;
+        o->cells = cells;
+        o->status = 0;
+        atomicMax(best_keys + cd.read, best_key(sc, c));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // a7: per-read decision from the per-read best keys.
 // ---------------------------------------------------------------------------
 __global__ void decide_kernel(rawalign_result_t *res, int n, const unsigned long long *keys,
@@ -223,6 +273,19 @@ cudaError_t launch_expected_signal(const SigDesc *d, int n, const uint8_t *ref2b
     } else {
         expected_signal_kernel<false><<<blocks, 256, 0, s>>>(d, n, ref32, pore, k, r_all);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const CombineDesc *d, int n, const PieceRef *plan, const rawalign_result_t *pieces,
+                           const float *events, const float *r_all, rawalign_result_t *results,
+                           unsigned long long *best_keys, float b_match, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    int blocks = (n + 127) / 128;
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    combine_kernel<<<blocks, 128, 0, s>>>(d, n, plan, pieces, events, r_all, results, best_keys, b_match);
     return cudaGetLastError();
 }
 

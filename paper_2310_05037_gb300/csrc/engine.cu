@@ -33,8 +33,49 @@ T *take(rawalign_dtw *h, Batch &b, uint64_t count)
     return (T *)p;
 }
 
+// One DTW work item: rows from event ev0 on (n of them) against the m
+// expected values from r0 on, result slot `slot`, per-read key slot `read`.
+void fill_work(PlanItem &it, uint64_t ev0, uint64_t r0, int64_t n, int64_t m, const BandDef &band, int32_t wrep,
+               int32_t slot, int32_t read, int32_t n_read)
+{
+    memset(&it.wd, 0, sizeof(WorkDesc));
+    WorkDesc &wd = it.wd;
+    wd.ev_off = ev0;
+    wd.r_off = r0;
+    wd.fin_off = ~0ull;
+    wd.num = band.num;
+    wd.den = band.den;
+    wd.row0 = 0;
+    wd.nrows = (int32_t)n;
+    wd.m = (int32_t)m;
+    wd.w = (int32_t)band.w;
+    wd.cand = slot;
+    wd.read = read;
+    wd.n_read = n_read;
+    wd.fin_lo = -1;
+    wd.fin_wid = 0;
+    wd.w_report = wrep;
+}
+
+// Anchors of one candidate are valid when sorted, disjoint in both sequences,
+// non-empty and inside the n x m table.
+bool anchors_valid(const rawalign_anchor_t *A, uint64_t K, int64_t n, int64_t m)
+{
+    int64_t pq = 0, pt = 0;
+    for (uint64_t a = 0; a < K; ++a) {
+        if (A[a].len < 1 || (int64_t)A[a].q < pq || (int64_t)A[a].t < pt)
+            return false;
+        pq = (int64_t)A[a].q + A[a].len;
+        pt = (int64_t)A[a].t + A[a].len;
+        if (pq > n || pt > m)
+            return false;
+    }
+    return true;
+}
+
 int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64_t *offs,
-                    uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands)
+                    uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
+                    const rawalign_anchor_t *anchors = nullptr, const uint64_t *anchor_offs = nullptr)
 {
     const int k = h->cfg.k;
     b.n_reads = n_reads;
@@ -49,11 +90,28 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         return RA_EINVAL;
     if (b.n_events >= (1ull << 40))
         return RA_EINVAL;
-    std::vector<PlanItem> items(n_cands);
+    b.anchored = anchor_offs != nullptr;
+    if (b.anchored && !anchors && n_cands && anchor_offs[n_cands] != anchor_offs[0])
+        return RA_EINVAL;
+    std::vector<PlanItem> items(b.anchored ? 0 : n_cands);
     std::vector<SigDesc> sig(n_cands);
+    std::vector<PieceRef> plan;
+    std::vector<CombineDesc> cdesc(b.anchored ? n_cands : 0);
     uint64_t r_total = 0;
     b.cells = 0;
     b.max_rows = 1;
+    const int forced = h->cfg.kernel >= RA_KERNEL_VARIANT0 ? h->cfg.kernel - RA_KERNEL_VARIANT0 : -1;
+    auto schedule_item = [&](PlanItem &it, const BandDef &band, int64_t n) {
+        Sched sc;
+        if (b.plain || (forced >= 0 && forced < kNumVariants)) {
+            it.variant = b.plain ? 0 : forced;
+            sc = schedule(band, 0, n, kVariants[it.variant][0], kVariants[it.variant][1]);
+        } else {
+            it.variant = choose_variant(band, 0, n, sc, h->slot_cost);
+        }
+        set_schedule(it, sc);
+        b.max_rows = std::max<int>(b.max_rows, (int)n);
+    };
     for (uint32_t c = 0; c < n_cands; ++c) {
         const rawalign_candidate_t &cd = cands[c];
         if (cd.read_id >= n_reads || cd.strand > 1)
@@ -70,40 +128,86 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         int32_t wrep;
         if (band_for(n, m, cd.band_w, cd.slope_num, cd.slope_den, band, wrep) != 0)
             return RA_EINVAL;
-        PlanItem &it = items[c];
-        memset(&it.wd, 0, sizeof(WorkDesc));
-        WorkDesc &wd = it.wd;
-        wd.ev_off = offs[cd.read_id];
-        wd.r_off = r_total;
-        wd.fin_off = ~0ull;
-        wd.num = band.num;
-        wd.den = band.den;
-        wd.row0 = 0;
-        wd.nrows = (int32_t)n;
-        wd.m = (int32_t)m;
-        wd.w = (int32_t)band.w;
-        wd.cand = (int32_t)c;
-        wd.read = (int32_t)cd.read_id;
-        wd.n_read = (int32_t)n;
-        wd.fin_lo = -1;
-        wd.fin_wid = 0;
-        wd.w_report = wrep;
-        Sched s;
-        const int forced = h->cfg.kernel >= RA_KERNEL_VARIANT0 ? h->cfg.kernel - RA_KERNEL_VARIANT0 : -1;
-        if (b.plain || (forced >= 0 && forced < kNumVariants)) {
-            it.variant = b.plain ? 0 : forced;
-            s = schedule(band, 0, n, kVariants[it.variant][0], kVariants[it.variant][1]);
+        const uint64_t ev0 = offs[cd.read_id];
+        if (!b.anchored) {
+            PlanItem &it = items[c];
+            fill_work(it, ev0, r_total, n, m, band, wrep, (int32_t)c, (int32_t)cd.read_id, (int32_t)n);
+            schedule_item(it, band, n);
         } else {
-            it.variant = choose_variant(band, 0, n, s, h->slot_cost);
+            // Sec. 2.4.2: gap 0, anchor 1, gap 1, ..., anchor K, gap K in path order
+            if (anchor_offs[c + 1] < anchor_offs[c])
+                return RA_EINVAL;
+            const rawalign_anchor_t *A = anchors ? anchors + anchor_offs[c] : nullptr;
+            const uint64_t K = anchor_offs[c + 1] - anchor_offs[c];
+            if (!anchors_valid(A, K, n, m))
+                return RA_EINVAL;
+            CombineDesc &cdc = cdesc[c];
+            cdc.first = (uint32_t)plan.size();
+            cdc.n = (int32_t)n;
+            cdc.m = (int32_t)m;
+            cdc.read = (int32_t)cd.read_id;
+            cdc.w_report = cd.band_w < 0 ? -1 : cd.band_w;
+            int64_t pq = 0, pt = 0;
+            for (uint64_t a = 0; a <= K; ++a) {
+                const int64_t q1 = a < K ? (int64_t)A[a].q : n, t1 = a < K ? (int64_t)A[a].t : m;
+                const int64_t nr = q1 - pq, nc = t1 - pt;
+                PieceRef pr{};
+                if (nr > 0 && nc > 0) {
+                    BandDef gb;
+                    int32_t gw;
+                    if (band_for(nr, nc, cd.band_w, 0, 0, gb, gw) != 0)
+                        return RA_EINVAL;
+                    PlanItem it;
+                    const int32_t slot = (int32_t)items.size();
+                    fill_work(it, ev0 + pq, r_total + pt, nr, nc, gb, gw, slot, slot, (int32_t)nr);
+                    schedule_item(it, gb, nr);
+                    items.push_back(it);
+                    pr.kind = 0;
+                    pr.idx = (uint32_t)slot;
+                    plan.push_back(pr);
+                } else if (nr > 0) {
+                    // events aligned to one value: the previous anchor's last (the first anchor's first)
+                    pr.kind = 1;
+                    pr.ev = ev0 + pq;
+                    pr.r = r_total + (a > 0 ? pt - 1 : t1);
+                    pr.len = (uint32_t)nr;
+                    pr.ev_step = 1;
+                    pr.r_step = 0;
+                    plan.push_back(pr);
+                } else if (nc > 0) {
+                    // values aligned to one event: the previous anchor's last (the first anchor's first)
+                    pr.kind = 1;
+                    pr.ev = ev0 + (a > 0 ? pq - 1 : q1);
+                    pr.r = r_total + pt;
+                    pr.len = (uint32_t)nc;
+                    pr.ev_step = 0;
+                    pr.r_step = 1;
+                    plan.push_back(pr);
+                }
+                if (a < K) {
+                    pr = PieceRef{};
+                    pr.kind = 1;
+                    pr.ev = ev0 + A[a].q;
+                    pr.r = r_total + A[a].t;
+                    pr.len = A[a].len;
+                    pr.ev_step = 1;
+                    pr.r_step = 1;
+                    plan.push_back(pr);
+                    pq = (int64_t)A[a].q + A[a].len;
+                    pt = (int64_t)A[a].t + A[a].len;
+                }
+            }
+            cdc.count = (uint32_t)plan.size() - cdc.first;
+            if (plan.size() >= (1ull << 32) || items.size() >= (1ull << 31))
+                return RA_EINVAL;
         }
-        set_schedule(it, s);
-        b.max_rows = std::max<int>(b.max_rows, (int)n);
         sig[c].ref_off = cd.ref_offset;
         sig[c].r_off = r_total;
         sig[c].len = cd.ref_len_bases;
         sig[c].strand = cd.strand;
         r_total += (uint64_t)m;
     }
+    b.n_work = (uint32_t)items.size();
     if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO)
         shorten_longest(items, h->sm_count, h->slot_cost);
     b.slots = 0;
@@ -116,17 +220,17 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         return RA_EINVAL;
     if (b.plain)
         b.classes.clear();
-    std::vector<WorkDesc> work(n_cands);
+    std::vector<WorkDesc> work(b.n_work);
+    for (uint32_t x = 0; x < b.n_work; ++x)
+        work[x] = items[order[x]].wd;
     std::vector<int> read_of(n_cands);
-    for (uint32_t c = 0; c < n_cands; ++c) {
-        work[c] = items[order[c]].wd;
+    for (uint32_t c = 0; c < n_cands; ++c)
         read_of[c] = (int)cands[c].read_id;
-    }
     // device memory
     b.d_events = take<float>(h, b, b.n_events);
     b.d_sig = take<SigDesc>(h, b, n_cands);
     b.d_r = take<float>(h, b, r_total);
-    b.d_work = take<WorkDesc>(h, b, n_cands);
+    b.d_work = take<WorkDesc>(h, b, b.n_work);
     b.d_results = take<rawalign_result_t>(h, b, n_cands);
     b.d_keys = take<unsigned long long>(h, b, n_reads);
     b.d_read_of = take<int>(h, b, n_cands);
@@ -135,6 +239,14 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         !b.d_queue)
         return RA_ENOMEM;
     b.d_err = b.d_queue + kMaxClasses;
+    if (b.anchored) {
+        b.d_pres = take<rawalign_result_t>(h, b, b.n_work);
+        b.d_pkeys = take<unsigned long long>(h, b, b.n_work);
+        b.d_plan = take<PieceRef>(h, b, plan.size());
+        b.d_cdesc = take<CombineDesc>(h, b, n_cands);
+        if (!b.d_pres || !b.d_pkeys || !b.d_plan || !b.d_cdesc)
+            return RA_ENOMEM;
+    }
     if (b.plain) {
         b.d_plain_diag = take<float>(h, b, 3ull * (b.max_rows + 2));
         if (!b.d_plain_diag)
@@ -147,7 +259,11 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     cudaStream_t s = h->stream;
     RA_CUDA(cudaMemcpyAsync(b.d_events, events, sizeof(float) * b.n_events, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_sig, sig.data(), sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
-    RA_CUDA(cudaMemcpyAsync(b.d_work, work.data(), sizeof(WorkDesc) * n_cands, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(b.d_work, work.data(), sizeof(WorkDesc) * b.n_work, cudaMemcpyHostToDevice, s));
+    if (b.anchored && !plan.empty())
+        RA_CUDA(cudaMemcpyAsync(b.d_plan, plan.data(), sizeof(PieceRef) * plan.size(), cudaMemcpyHostToDevice, s));
+    if (b.anchored && n_cands)
+        RA_CUDA(cudaMemcpyAsync(b.d_cdesc, cdesc.data(), sizeof(CombineDesc) * n_cands, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_read_of, read_of.data(), sizeof(int) * n_cands, cudaMemcpyHostToDevice, s));
     for (auto &e : b.ev)
         RA_CUDA(cudaEventCreate(&e));
@@ -170,10 +286,15 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
         RA_CUDA(launch_expected_signal(b.d_sig, (int)b.n_cands, h->d_ref, h->d_pore, h->cfg.k, b.d_r, s));
         launches += b.n_cands ? 1 : 0;
     } else if (part == 1) {
+        // anchored batches run their gaps as GLOBAL alignments into per-gap
+        // results, then combine them per candidate (Sec. 2.4.2)
+        rawalign_result_t *res = b.anchored ? b.d_pres : b.d_results;
+        unsigned long long *keys = b.anchored ? b.d_pkeys : b.d_keys;
+        const int end_free = !b.anchored && h->cfg.end_mode == RA_END_FREE;
         if (b.plain) {
-            for (uint32_t c = 0; c < b.n_cands; ++c) {
-                RA_CUDA(launch_plain(b.d_work + c, b.d_events, b.d_r, b.d_plain_diag, b.d_results, b.d_keys,
-                                     h->cfg.b_match, h->cfg.end_mode == RA_END_FREE, s));
+            for (uint32_t x = 0; x < b.n_work; ++x) {
+                RA_CUDA(launch_plain(b.d_work + x, b.d_events, b.d_r, b.d_plain_diag, res, keys, h->cfg.b_match,
+                                     end_free, s));
                 ++launches;
             }
         } else {
@@ -193,19 +314,24 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
                 p.r_all = b.d_r;
                 p.fstore = nullptr;
                 p.fstore_out = nullptr;
-                p.results = b.d_results;
-                p.best_keys = b.d_keys;
+                p.results = res;
+                p.best_keys = keys;
                 p.gring = cl.gring;
                 p.ring_cap = cl.ring_cap;
                 p.ring_in_smem = cl.ring_in_smem;
                 p.b_match = h->cfg.b_match;
-                p.end_free = h->cfg.end_mode == RA_END_FREE;
+                p.end_free = end_free;
                 p.err = b.d_err;
                 RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
                 ++launches;
                 RA_CUDA(cudaEventRecord(h->join[ci], cs));
                 RA_CUDA(cudaStreamWaitEvent(s, h->join[ci], 0));
             }
+        }
+        if (b.anchored) {
+            RA_CUDA(launch_combine(b.d_cdesc, (int)b.n_cands, b.d_plan, b.d_pres, b.d_events, b.d_r, b.d_results,
+                                   b.d_keys, h->cfg.b_match, s));
+            launches += b.n_cands ? 1 : 0;
         }
     } else {
         RA_CUDA(launch_decide(b.d_results, (int)b.n_cands, b.d_keys, b.d_read_of, h->cfg.score_threshold, 1, s));
@@ -379,6 +505,49 @@ extern "C" int rawalign_dtw_prepare_batch(rawalign_dtw_t *h, const float *events
     }
     *batch = id;
     return RA_OK;
+}
+
+extern "C" int rawalign_dtw_prepare_anchored(rawalign_dtw_t *h, const float *events, const uint64_t *read_offsets,
+                                             uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
+                                             const rawalign_anchor_t *anchors, const uint64_t *anchor_offsets,
+                                             uint64_t *batch)
+{
+    if (!h || !batch || !read_offsets || !anchor_offsets || (n_cands && !cands) || (!events && n_reads))
+        return RA_EINVAL;
+    cudaSetDevice(h->device);
+    uint64_t id = h->next_id++;
+    Batch &b = h->batches[id];
+    int rc = plan_and_upload(h, b, events, read_offsets, n_reads, cands, n_cands, anchors, anchor_offsets);
+    if (rc != RA_OK) {
+        free_batch(h, b);
+        h->batches.erase(id);
+        return rc;
+    }
+    *batch = id;
+    return RA_OK;
+}
+
+extern "C" int rawalign_dtw_submit_anchored(rawalign_dtw_t *h, const float *events, const uint64_t *read_offsets,
+                                            uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
+                                            const rawalign_anchor_t *anchors, const uint64_t *anchor_offsets,
+                                            uint64_t *ticket)
+{
+    if (!ticket)
+        return RA_EINVAL;
+    uint64_t bid = 0;
+    int rc = rawalign_dtw_prepare_anchored(h, events, read_offsets, n_reads, cands, n_cands, anchors,
+                                           anchor_offsets, &bid);
+    if (rc != RA_OK)
+        return rc;
+    Batch &b = h->batches[bid];
+    b.auto_release = true;
+    rc = record_run(h, b);
+    if (rc != RA_OK) {
+        rawalign_dtw_release_batch(h, bid);
+        return rc;
+    }
+    b.ran = true;
+    return new_ticket(h, bid, b, ticket);
 }
 
 extern "C" int rawalign_dtw_run_batch(rawalign_dtw_t *h, uint64_t batch, uint64_t *ticket)

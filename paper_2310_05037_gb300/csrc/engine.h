@@ -202,6 +202,12 @@ struct Batch {
     int *d_err = nullptr;    // [2]
     float *d_plain_diag = nullptr;
     int max_rows = 0;
+    uint32_t n_work = 0;                    // DTW work items (candidates, or gaps when anchored)
+    bool anchored = false;                  // anchor-guided batch (Sec. 2.4.2)
+    rawalign_result_t *d_pres = nullptr;    // anchored: per-gap DTW results
+    unsigned long long *d_pkeys = nullptr;  // anchored: per-gap keys (unused by the decision)
+    PieceRef *d_plan = nullptr;             // anchored: pieces of every candidate in path order
+    CombineDesc *d_cdesc = nullptr;         // anchored: per-candidate piece range and table size
     std::vector<ClassLaunch> classes;
     uint64_t cells = 0;
     bool auto_release = false;

@@ -66,6 +66,28 @@ struct StripeParams {
     int *err;                      // error word (first failing work item + 1)
 };
 
+// Anchor-guided alignment (Sec. 2.4.2): one candidate's cost is the sum, in
+// path order, of its pieces: gaps aligned by their own DTW (kind 0, result
+// of work item idx) and runs of cells summed directly (kind 1: an anchor's
+// diagonal, ev_step = r_step = 1; a gap with rows only, r_step = 0; a gap
+// with columns only, ev_step = 0).
+struct PieceRef {
+    uint64_t ev;      // first event (index in the events array)
+    uint64_t r;       // first expected value (index in r_all)
+    uint32_t kind;    // 0: DTW gap, 1: run of cells
+    uint32_t len;     // cells of a run
+    uint32_t idx;     // work item of a DTW gap
+    uint16_t ev_step, r_step;
+};
+static_assert(sizeof(PieceRef) == 32, "PieceRef layout");
+
+struct CombineDesc {
+    uint32_t first, count;  // pieces of the candidate in the plan array
+    int32_t n, m;           // table size (N_Read = n)
+    int32_t read;           // read slot for the per-read best
+    int32_t w_report;       // half-width reported (-1 = no band)
+};
+
 // Host-side launchers (dtw_kernels.cu).
 cudaError_t launch_expected_signal(const SigDesc *d, int n, const uint8_t *ref2bit, const float *pore,
                                    int k, float *r_all, cudaStream_t s);
@@ -78,6 +100,9 @@ cudaError_t launch_plain(const WorkDesc *w, const float *events, const float *r_
                          int end_free, cudaStream_t s);
 int host_band(int64_t n, int64_t m, int32_t band_w, int64_t num, int64_t den, int64_t *num_out,
               int64_t *den_out, int64_t *w_out, int32_t *w_report);
+cudaError_t launch_combine(const CombineDesc *d, int n, const PieceRef *plan, const rawalign_result_t *pieces,
+                           const float *events, const float *r_all, rawalign_result_t *results,
+                           unsigned long long *best_keys, float b_match, cudaStream_t s);
 cudaError_t launch_decide(rawalign_result_t *results, int n, const unsigned long long *best_keys,
                           const int *read_of, float thr, int final_decision, cudaStream_t s);
 

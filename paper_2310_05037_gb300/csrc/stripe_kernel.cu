@@ -105,7 +105,11 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
     bool done = true, exhausted = false, have = false;
 
     // set-up of this lane's rows for stripe k (row-wise band DDA from the
-    // lane's first row, kept in shared memory)
+    // lane's first row, kept in shared memory).  The DP column and the
+    // diagonal are not reset: a lane enters a stripe at least one column
+    // before the first in-band column of its rows (the period dC guarantees
+    // it), so its first step there has every row out of band, d = +inf, and
+    // every value of the column becomes +inf whatever the old registers held.
     auto setup_stripe = [&]() {
         const int nrows = gc->nrows, K = gc->K, den = gc->den, q1 = gc->q1, r1 = gc->r1;
         const float *ev = gc->ev;
@@ -136,7 +140,6 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                 lo[r] = kBigCol;
                 wid[r] = 0;
             }
-            D[r] = kInf;
             Ql += q1;
             Rl += r1;
             if (Rl >= den) {
@@ -175,7 +178,6 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         }
         writer = (t == G - 1) && (k < K - 1);
         holds_last = (k == K - 1) && (t == gc->t_last);
-        diag = kInf;
         if (FREE_END && holds_last) {
             r_last = gc->r_last;
             lastLo = kBigCol;

@@ -26,6 +26,8 @@ import numpy as np
 
 K = 6
 N_KMERS = 4 ** K
+# one anchor of a chain: events q..q+len-1 on the diagonal with expected values t..t+len-1
+ANCHOR_DTYPE = np.dtype([("q", "<u4"), ("t", "<u4"), ("len", "<u4")])
 
 CANDIDATE_DTYPE = np.dtype(
     {
@@ -127,21 +129,26 @@ def _kmer_means(codes: np.ndarray, pore: np.ndarray) -> np.ndarray:
     return pore[idx]
 
 
-def simulate_events(rng, codes, pore, n_events, noise_sd, skip, stay=0.0, mean_dwell=1.1):
+def simulate_events(rng, codes, pore, n_events, noise_sd, skip, stay=0.0, mean_dwell=1.1, return_source=False):
     """Walk the k-mers of ``codes``; each emits Geometric(mean mean_dwell)
     events, or none with probability ``skip``; each event is repeated once
     with probability ``stay``; value = k-mer mean + N(0, noise_sd).
-    Returns at most n_events values (fewer if the walk runs out)."""
+    Returns at most n_events values (fewer if the walk runs out), and with
+    ``return_source`` also the index of the k-mer each event came from."""
     means = _kmer_means(codes, pore)
     p = 1.0 / mean_dwell
     cnt = rng.geometric(p, size=len(means))
     cnt[rng.random(len(means)) < skip] = 0
     ev_mean = np.repeat(means, cnt)
+    src = np.repeat(np.arange(len(means)), cnt)
     if stay > 0:
         dup = rng.random(len(ev_mean)) < stay
         ev_mean = np.repeat(ev_mean, 1 + dup.astype(np.int64))
+        src = np.repeat(src, 1 + dup.astype(np.int64))
     ev_mean = ev_mean[:n_events]
     ev = ev_mean + rng.normal(0.0, noise_sd, size=len(ev_mean))
+    if return_source:
+        return ev.astype(np.float32), src[:n_events]
     return ev.astype(np.float32)
 
 
@@ -159,6 +166,8 @@ class Workload:
     b_match: float = 0.4
     score_threshold: float = 20.0
     meta: dict = dataclasses.field(default_factory=dict)
+    anchors: np.ndarray | None = None         # ANCHOR_DTYPE, all candidates' chains back to back
+    anchor_offsets: np.ndarray | None = None  # n_cands + 1 offsets into anchors
 
     @property
     def n_reads(self) -> int:
@@ -181,8 +190,15 @@ class Workload:
         offs[1:] = np.cumsum(lens)
         ev = np.concatenate([self.events[self.read_offsets[r] : self.read_offsets[r + 1]] for r in reads])
         sel["read_id"] = inv.astype(np.uint64)
+        anchors = aoffs = None
+        if self.anchor_offsets is not None:
+            parts = [self.anchors[self.anchor_offsets[c] : self.anchor_offsets[c + 1]] for c in cand_idx]
+            aoffs = np.zeros(len(cand_idx) + 1, np.uint64)
+            aoffs[1:] = np.cumsum([len(a) for a in parts])
+            anchors = np.concatenate(parts) if parts else np.zeros(0, ANCHOR_DTYPE)
         return dataclasses.replace(self, events=ev.astype(np.float32), read_offsets=offs, cands=sel,
-                                   meta=dict(self.meta, subset=len(cand_idx)))
+                                   meta=dict(self.meta, subset=len(cand_idx)), anchors=anchors,
+                                   anchor_offsets=aoffs)
 
 
 def _make_cands(n):
@@ -268,6 +284,90 @@ def config_batched(seed: int = 0x5EED0002, n_reads: int = 20_000, ref_len: int =
             rows.append((q, off, span, 0, w, 0, 0))
     return _finish("batched_uneven", pore, ref, ref_len, reads, rows,
                    dict(config=2, seed=seed, n_reads=n_reads, ref_len=ref_len))
+
+
+def true_anchors(src, n, m, min_len=8, max_len=16, every=2):
+    """Anchors from a simulated read's event -> k-mer map: runs of events
+    that step one k-mer per event (as a seed match would cover them), cut to
+    at most max_len, every ``every``-th run kept, inside the n x m table."""
+    out = []
+    i = 0
+    run = 0
+    while i < n:
+        j = i
+        while j + 1 < n and src[j + 1] == src[j] + 1:
+            j += 1
+        ln = j - i + 1
+        if ln >= min_len:
+            if run % every == 0:
+                ln = min(ln, max_len)
+                t = int(src[i])
+                if t + ln <= m:
+                    out.append((i, t, ln))
+            run += 1
+        i = j + 1
+    return out
+
+
+def decoy_anchors(rng, n, m, k_max=6, min_len=4, max_len=12):
+    """A random chain for a decoy locus: sorted, disjoint anchors scattered
+    around the table's diagonal."""
+    out = []
+    pq = pt = 0
+    qs = np.sort(rng.integers(0, n, size=int(rng.integers(0, k_max + 1))))
+    for q in qs:
+        q = int(max(q, pq))
+        t = int(max(pt, min(m - 1, round(q * m / n + rng.integers(-8, 9)))))
+        ln = int(rng.integers(min_len, max_len + 1))
+        ln = min(ln, n - q, m - t)
+        if ln < 1:
+            continue
+        out.append((q, t, ln))
+        pq, pt = q + ln, t + ln
+    return out
+
+
+def config_anchored(seed: int = 0x5EED0006, n_reads: int = 20_000, ref_len: int = 100_000_000,
+                    median: int = 1500, sigma: float = 0.6, lo: int = 200, hi: int = 8000,
+                    max_cands: int = 8, band_frac: float = 0.10) -> Workload:
+    """Anchor-guided batch (Sec. 2.4.2): the batched-uneven shapes, and each
+    candidate carries a chain: the true locus's anchors come from the
+    simulated read's event -> k-mer map, decoys get random chains."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pore = pore_table(seed ^ 0xA5A5)
+    ref = hashed_reference(seed, ref_len)
+    lens = _lognormal_lengths(rng, n_reads, median, sigma, lo, hi)
+    reads, rows, chains = [], [], []
+    for q in range(n_reads):
+        n = int(lens[q])
+        while True:
+            loc = int(rng.integers(0, ref_len - 3 * n - 64))
+            walk = unpack_bases(ref, loc, 2 * n + K)
+            ev, src = simulate_events(rng, walk, pore, n, 0.3, 0.05, return_source=True)
+            if len(ev) == n:
+                break
+        reads.append(ev)
+        nc = int(rng.integers(1, max_cands + 1))
+        true_slot = int(rng.integers(0, nc))
+        for c in range(nc):
+            m = int(math.floor(n * rng.uniform(0.9, 1.3)))
+            span = m + K - 1
+            if c == true_slot:
+                off = loc
+                chains.append(true_anchors(src, n, m))
+            else:
+                off = int(rng.integers(0, ref_len - span))
+                chains.append(decoy_anchors(rng, n, m))
+            w = int(math.floor(band_frac * m))
+            rows.append((q, off, span, 0, w, 0, 0))
+    wl = _finish("anchored", pore, ref, ref_len, reads, rows,
+                 dict(config="anchored", seed=seed, n_reads=n_reads, ref_len=ref_len))
+    aoffs = np.zeros(len(chains) + 1, np.uint64)
+    aoffs[1:] = np.cumsum([len(ch) for ch in chains])
+    flat = [a for ch in chains for a in ch]
+    wl.anchors = np.array(flat, dtype=ANCHOR_DTYPE) if flat else np.zeros(0, ANCHOR_DTYPE)
+    wl.anchor_offsets = aoffs
+    return wl
 
 
 def config_readuntil(seed: int = 0x5EED0003, n_reads: int = 100_000, ref_len: int = 3_000_000_000,
@@ -403,6 +503,10 @@ def scaled(name: str, scale: str = "full", seed: int | None = None) -> Workload:
         if scale == "full":
             return config_readuntil(**kw)
         return config_readuntil(n_reads=24, ref_len=4_000_000, cmin=4, cmax=12, **kw)
+    if name == "anchored":
+        if scale == "full":
+            return config_anchored(**kw)
+        return config_anchored(n_reads=40, ref_len=2_000_000, median=400, lo=60, hi=1500, **kw)
     if name == "longread":
         if scale == "full":
             return config_longread(**kw)

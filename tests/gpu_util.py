@@ -138,3 +138,61 @@ def edge_workload(seed=7, k=6):
     add(300, 300, bw=10, exact=True)
     add(300, 300, bw=-1, exact=True, strand=1)
     return S._finish("edges", pore, ref, ref_len, reads, rows, dict(seed=seed))
+
+
+def run_gpu_anchored(w: S.Workload, kernel=B.RA_KERNEL_AUTO, graph_runs=0, **kw):
+    """Anchor-guided batch through rawalign_dtw_submit_anchored (or, with
+    graph_runs, prepare_anchored + replays)."""
+    arena = arena_bytes_for(w) + 256 * (len(w.anchors) + w.n_cands) * 4
+    al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=(arena + 255) // 256 * 256, k=w.k,
+                   b_match=w.b_match, score_threshold=w.score_threshold, kernel=kernel, **kw)
+    try:
+        if graph_runs:
+            b = al.prepare_anchored(w.events, w.read_offsets, w.cands, w.anchors, w.anchor_offsets)
+            outs = [al.poll(al.run(b), w.n_cands) for _ in range(graph_runs)]
+            al.release(b)
+            return outs
+        return al.align_anchored(w.events, w.read_offsets, w.cands, w.anchors, w.anchor_offsets)
+    finally:
+        al.close()
+
+
+def run_oracle_anchored(w: S.Workload, use_f64=False):
+    return O.map_anchored(w.k, w.b_match, w.score_threshold, w.pore, w.ref2bit, w.ref_len, w.events,
+                          w.read_offsets, w.cands, w.anchors, w.anchor_offsets, use_f64=use_f64)
+
+
+def tiny_anchored_workload(seed, n_cands=2000, max_n=12, max_m=12, k=6):
+    """Small tables with random chains: anchors at the corners, adjacent
+    anchors, gaps with rows only or columns only, empty chains; random and
+    integer-valued events; both strands."""
+    rng = np.random.default_rng(seed)
+    pore = S.pore_table(seed)
+    ref_len = 20000
+    ref = S.hashed_reference(seed + 1, ref_len)
+    reads, rows, chains = [], [], []
+    for c in range(n_cands):
+        n = int(rng.integers(1, max_n + 1))
+        m = int(rng.integers(1, max_m + 1))
+        ev = rng.normal(size=n) if rng.random() < 0.6 else rng.integers(-2, 3, size=n).astype(np.float64)
+        reads.append(ev.astype(np.float32))
+        span = m + k - 1
+        rows.append((c, int(rng.integers(0, ref_len - span)), span, int(rng.random() < 0.3),
+                     int(rng.integers(-1, 6)), 0, 0))
+        chain, q, t = [], 0, 0
+        for _ in range(int(rng.integers(0, 4))):
+            if q >= n or t >= m:
+                break
+            q0 = int(rng.integers(q, min(n, q + 4)))
+            t0 = int(rng.integers(t, min(m, t + 4)))
+            ln = int(rng.integers(1, min(n - q0, m - t0) + 1))
+            chain.append((q0, t0, ln))
+            q, t = q0 + ln, t0 + ln
+        chains.append(chain)
+    w = S._finish("tiny_anchored", pore, ref, ref_len, reads, rows, dict(seed=seed))
+    aoffs = np.zeros(n_cands + 1, np.uint64)
+    aoffs[1:] = np.cumsum([len(ch) for ch in chains])
+    flat = [a for ch in chains for a in ch]
+    w.anchors = np.array(flat, dtype=S.ANCHOR_DTYPE) if flat else np.zeros(0, S.ANCHOR_DTYPE)
+    w.anchor_offsets = aoffs
+    return w

@@ -54,8 +54,10 @@ def _c_layout():
 #include "rawalign_dtw.h"
 #define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
 int main(void) {
-  printf("cand %zu\nres %zu\ncfg %zu\nstats %zu\n", sizeof(rawalign_candidate_t), sizeof(rawalign_result_t),
-         sizeof(rawalign_dtw_config_t), sizeof(rawalign_dtw_stats_t));
+  printf("cand %zu\nres %zu\ncfg %zu\nstats %zu\nanchor %zu\n", sizeof(rawalign_candidate_t),
+         sizeof(rawalign_result_t), sizeof(rawalign_dtw_config_t), sizeof(rawalign_dtw_stats_t),
+         sizeof(rawalign_anchor_t));
+  O(rawalign_anchor_t, q); O(rawalign_anchor_t, t); O(rawalign_anchor_t, len);
   O(rawalign_candidate_t, read_id); O(rawalign_candidate_t, ref_offset); O(rawalign_candidate_t, ref_len_bases);
   O(rawalign_candidate_t, strand); O(rawalign_candidate_t, band_w); O(rawalign_candidate_t, slope_num);
   O(rawalign_candidate_t, slope_den);
@@ -82,10 +84,14 @@ def test_record_layouts_agree():
     assert int(lay["res"]) == C.sizeof(B.Result) == B.RESULT_DTYPE.itemsize == 56
     assert int(lay["cfg"]) == C.sizeof(B.Config)
     assert int(lay["stats"]) == C.sizeof(B.Stats)
+    assert int(lay["anchor"]) == B.ANCHOR_DTYPE.itemsize == S.ANCHOR_DTYPE.itemsize == C.sizeof(O.Anchor) == 12
     for k, v in lay.items():
         if "." not in k:
             continue
         T, f = k.split(".")
+        if T == "rawalign_anchor_t":
+            assert S.ANCHOR_DTYPE.fields[f][1] == int(v) == getattr(O.Anchor, f).offset, k
+            continue
         py = {"rawalign_candidate_t": B.Candidate, "rawalign_result_t": B.Result, "rawalign_dtw_config_t": B.Config}[T]
         assert getattr(py, f).offset == int(v), k
         if T == "rawalign_candidate_t":

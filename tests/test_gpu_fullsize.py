@@ -179,3 +179,29 @@ def test_full_longread():
         cost = float(g["cost"][c])
         tol = steps * U32
         assert lower * (1 - tol) <= cost <= upper * (1 + tol), (c, lower, cost, upper)
+
+
+def test_full_anchored():
+    """Anchor-guided batch at the batched workload's full size (Sec. 2.4.2)."""
+    from gpu_util import run_gpu_anchored
+
+    w = S.scaled("anchored", "full")
+    a, b = run_gpu_anchored(w, graph_runs=2)
+    for f in a.dtype.names:
+        assert np.array_equal(a[f], b[f]), f
+    _check_properties(w, a)
+    rng = np.random.default_rng(23)
+    lens = w.read_lengths()
+    reads = set(rng.choice(w.n_reads, 40, replace=False).tolist()) | {int(np.argmax(lens))}
+    idx = _whole_reads(w, sorted(reads))
+    sub = w.subset(idx)
+    args = (sub.k, sub.b_match, sub.score_threshold, sub.pore, sub.ref2bit, sub.ref_len, sub.events,
+            sub.read_offsets, sub.cands, sub.anchors, sub.anchor_offsets)
+    o = O.map_anchored(*args)
+    gs = a[idx]
+    assert np.array_equal(gs["cost"].view(np.uint32), o["cost"].astype(np.float32).view(np.uint32))
+    assert np.array_equal(gs["score"].view(np.uint32), o["score"].astype(np.float32).view(np.uint32))
+    for f in ("end_i", "end_j", "w_eff", "cells", "is_best", "decision"):
+        assert np.array_equal(gs[f].astype(np.int64), o[f].astype(np.int64)), f
+    c64 = O.map_anchored(*args, use_f64=True)["cost64"]
+    assert (np.abs(gs["cost"].astype(np.float64) - c64) / np.maximum(c64, 1e-30)).max() < 1e-5
