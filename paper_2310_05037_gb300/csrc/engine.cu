@@ -97,21 +97,9 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     std::vector<SigDesc> sig(n_cands);
     std::vector<PieceRef> plan;
     std::vector<CombineDesc> cdesc(b.anchored ? n_cands : 0);
+    // pass 1 (sequential, cheap): candidate checks and each candidate's row
+    // of expected values in the packed r array
     uint64_t r_total = 0;
-    b.cells = 0;
-    b.max_rows = 1;
-    const int forced = h->cfg.kernel >= RA_KERNEL_VARIANT0 ? h->cfg.kernel - RA_KERNEL_VARIANT0 : -1;
-    auto schedule_item = [&](PlanItem &it, const BandDef &band, int64_t n) {
-        Sched sc;
-        if (b.plain || (forced >= 0 && forced < kNumVariants)) {
-            it.variant = b.plain ? 0 : forced;
-            sc = schedule(band, 0, n, kVariants[it.variant][0], kVariants[it.variant][1]);
-        } else {
-            it.variant = choose_variant(band, 0, n, sc, h->slot_cost);
-        }
-        set_schedule(it, sc);
-        b.max_rows = std::max<int>(b.max_rows, (int)n);
-    };
     for (uint32_t c = 0; c < n_cands; ++c) {
         const rawalign_candidate_t &cd = cands[c];
         if (cd.read_id >= n_reads || cd.strand > 1)
@@ -124,25 +112,65 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         const int64_t m = (int64_t)cd.ref_len_bases - k + 1;
         if (n >= (1 << 30) || m >= (1 << 30))
             return RA_EINVAL;
-        BandDef band;
-        int32_t wrep;
-        if (band_for(n, m, cd.band_w, cd.slope_num, cd.slope_den, band, wrep) != 0)
+        if (b.anchored && anchor_offs[c + 1] < anchor_offs[c])
             return RA_EINVAL;
-        const uint64_t ev0 = offs[cd.read_id];
-        if (!b.anchored) {
-            PlanItem &it = items[c];
-            fill_work(it, ev0, r_total, n, m, band, wrep, (int32_t)c, (int32_t)cd.read_id, (int32_t)n);
-            schedule_item(it, band, n);
-        } else {
+        sig[c].ref_off = cd.ref_offset;
+        sig[c].r_off = r_total;
+        sig[c].len = cd.ref_len_bases;
+        sig[c].strand = cd.strand;
+        r_total += (uint64_t)m;
+    }
+    // pass 2 (threads over candidate ranges): band, work items and schedules;
+    // anchored chains are cut into pieces in thread-local lists, merged after
+    b.cells = 0;
+    b.max_rows = 1;
+    const int forced = h->cfg.kernel >= RA_KERNEL_VARIANT0 ? h->cfg.kernel - RA_KERNEL_VARIANT0 : -1;
+    struct Part {
+        uint32_t c0 = 0, c1 = 0;
+        std::vector<PlanItem> items;
+        std::vector<PieceRef> plan;
+        int max_rows = 1;
+        int rc = RA_OK;
+    };
+    auto plan_range = [&](Part &pt_) {
+        auto schedule_item = [&](PlanItem &it, const BandDef &band, int64_t n) {
+            Sched sc;
+            if (b.plain || (forced >= 0 && forced < kNumVariants)) {
+                it.variant = b.plain ? 0 : forced;
+                sc = schedule(band, 0, n, kVariants[it.variant][0], kVariants[it.variant][1]);
+            } else {
+                it.variant = choose_variant(band, 0, n, sc, h->slot_cost);
+            }
+            set_schedule(it, sc);
+            pt_.max_rows = std::max<int>(pt_.max_rows, (int)n);
+        };
+        for (uint32_t c = pt_.c0; c < pt_.c1; ++c) {
+            const rawalign_candidate_t &cd = cands[c];
+            const int64_t n = (int64_t)(offs[cd.read_id + 1] - offs[cd.read_id]);
+            const int64_t m = (int64_t)cd.ref_len_bases - k + 1;
+            const uint64_t r0 = sig[c].r_off;
+            BandDef band;
+            int32_t wrep;
+            if (band_for(n, m, cd.band_w, cd.slope_num, cd.slope_den, band, wrep) != 0) {
+                pt_.rc = RA_EINVAL;
+                return;
+            }
+            const uint64_t ev0 = offs[cd.read_id];
+            if (!b.anchored) {
+                PlanItem &it = items[c];
+                fill_work(it, ev0, r0, n, m, band, wrep, (int32_t)c, (int32_t)cd.read_id, (int32_t)n);
+                schedule_item(it, band, n);
+                continue;
+            }
             // Sec. 2.4.2: gap 0, anchor 1, gap 1, ..., anchor K, gap K in path order
-            if (anchor_offs[c + 1] < anchor_offs[c])
-                return RA_EINVAL;
             const rawalign_anchor_t *A = anchors ? anchors + anchor_offs[c] : nullptr;
             const uint64_t K = anchor_offs[c + 1] - anchor_offs[c];
-            if (!anchors_valid(A, K, n, m))
-                return RA_EINVAL;
+            if (!anchors_valid(A, K, n, m)) {
+                pt_.rc = RA_EINVAL;
+                return;
+            }
             CombineDesc &cdc = cdesc[c];
-            cdc.first = (uint32_t)plan.size();
+            cdc.first = (uint32_t)pt_.plan.size();  // part-local until the merge
             cdc.n = (int32_t)n;
             cdc.m = (int32_t)m;
             cdc.read = (int32_t)cd.read_id;
@@ -155,57 +183,97 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
                 if (nr > 0 && nc > 0) {
                     BandDef gb;
                     int32_t gw;
-                    if (band_for(nr, nc, cd.band_w, 0, 0, gb, gw) != 0)
-                        return RA_EINVAL;
+                    if (band_for(nr, nc, cd.band_w, 0, 0, gb, gw) != 0) {
+                        pt_.rc = RA_EINVAL;
+                        return;
+                    }
                     PlanItem it;
-                    const int32_t slot = (int32_t)items.size();
-                    fill_work(it, ev0 + pq, r_total + pt, nr, nc, gb, gw, slot, slot, (int32_t)nr);
+                    const int32_t slot = (int32_t)pt_.items.size();  // part-local until the merge
+                    fill_work(it, ev0 + pq, r0 + pt, nr, nc, gb, gw, slot, slot, (int32_t)nr);
                     schedule_item(it, gb, nr);
-                    items.push_back(it);
+                    pt_.items.push_back(it);
                     pr.kind = 0;
                     pr.idx = (uint32_t)slot;
-                    plan.push_back(pr);
+                    pt_.plan.push_back(pr);
                 } else if (nr > 0) {
                     // events aligned to one value: the previous anchor's last (the first anchor's first)
                     pr.kind = 1;
                     pr.ev = ev0 + pq;
-                    pr.r = r_total + (a > 0 ? pt - 1 : t1);
+                    pr.r = r0 + (a > 0 ? pt - 1 : t1);
                     pr.len = (uint32_t)nr;
                     pr.ev_step = 1;
                     pr.r_step = 0;
-                    plan.push_back(pr);
+                    pt_.plan.push_back(pr);
                 } else if (nc > 0) {
                     // values aligned to one event: the previous anchor's last (the first anchor's first)
                     pr.kind = 1;
                     pr.ev = ev0 + (a > 0 ? pq - 1 : q1);
-                    pr.r = r_total + pt;
+                    pr.r = r0 + pt;
                     pr.len = (uint32_t)nc;
                     pr.ev_step = 0;
                     pr.r_step = 1;
-                    plan.push_back(pr);
+                    pt_.plan.push_back(pr);
                 }
                 if (a < K) {
                     pr = PieceRef{};
                     pr.kind = 1;
                     pr.ev = ev0 + A[a].q;
-                    pr.r = r_total + A[a].t;
+                    pr.r = r0 + A[a].t;
                     pr.len = A[a].len;
                     pr.ev_step = 1;
                     pr.r_step = 1;
-                    plan.push_back(pr);
+                    pt_.plan.push_back(pr);
                     pq = (int64_t)A[a].q + A[a].len;
                     pt = (int64_t)A[a].t + A[a].len;
                 }
             }
-            cdc.count = (uint32_t)plan.size() - cdc.first;
-            if (plan.size() >= (1ull << 32) || items.size() >= (1ull << 31))
-                return RA_EINVAL;
+            cdc.count = (uint32_t)pt_.plan.size() - cdc.first;
         }
-        sig[c].ref_off = cd.ref_offset;
-        sig[c].r_off = r_total;
-        sig[c].len = cd.ref_len_bases;
-        sig[c].strand = cd.strand;
-        r_total += (uint64_t)m;
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const uint32_t n_parts = std::max<uint32_t>(1, std::min<uint32_t>(std::min(hw, 16u), (n_cands + 4095) / 4096));
+    std::vector<Part> parts(n_parts);
+    for (uint32_t t = 0; t < n_parts; ++t) {
+        parts[t].c0 = (uint32_t)((uint64_t)n_cands * t / n_parts);
+        parts[t].c1 = (uint32_t)((uint64_t)n_cands * (t + 1) / n_parts);
+    }
+    if (n_parts == 1) {
+        plan_range(parts[0]);
+    } else {
+        std::vector<std::thread> th;
+        for (uint32_t t = 0; t < n_parts; ++t)
+            th.emplace_back(plan_range, std::ref(parts[t]));
+        for (auto &x : th)
+            x.join();
+    }
+    uint64_t n_items = 0, n_plan = 0;
+    for (auto &pt_ : parts) {
+        if (pt_.rc != RA_OK)
+            return pt_.rc;
+        b.max_rows = std::max(b.max_rows, pt_.max_rows);
+        n_items += pt_.items.size();
+        n_plan += pt_.plan.size();
+    }
+    if (b.anchored) {
+        if (n_plan >= (1ull << 32) || n_items >= (1ull << 31))
+            return RA_EINVAL;
+        items.reserve(n_items);
+        plan.reserve(n_plan);
+        for (auto &pt_ : parts) {
+            const uint32_t ibase = (uint32_t)items.size(), pbase = (uint32_t)plan.size();
+            for (auto &it : pt_.items) {
+                it.wd.cand += (int32_t)ibase;
+                it.wd.read += (int32_t)ibase;
+                items.push_back(it);
+            }
+            for (auto pr : pt_.plan) {
+                if (pr.kind == 0)
+                    pr.idx += ibase;
+                plan.push_back(pr);
+            }
+            for (uint32_t c = pt_.c0; c < pt_.c1; ++c)
+                cdesc[c].first += pbase;
+        }
     }
     b.n_work = (uint32_t)items.size();
     if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO)
@@ -256,7 +324,10 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     int rc = finalize_classes(h->sm_count, b.classes, [&](uint64_t bytes) { return (void *)take<char>(h, b, bytes); });
     if (rc != RA_OK)
         return rc;
-    cudaStream_t s = h->stream;
+    // uploads go on their own stream so that planning and copying this batch
+    // overlap the kernels of the batch before it; the handle's stream waits
+    // for them, and the host only for the copies themselves
+    cudaStream_t s = h->upload;
     RA_CUDA(cudaMemcpyAsync(b.d_events, events, sizeof(float) * b.n_events, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_sig, sig.data(), sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_work, work.data(), sizeof(WorkDesc) * b.n_work, cudaMemcpyHostToDevice, s));
@@ -267,8 +338,10 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     RA_CUDA(cudaMemcpyAsync(b.d_read_of, read_of.data(), sizeof(int) * n_cands, cudaMemcpyHostToDevice, s));
     for (auto &e : b.ev)
         RA_CUDA(cudaEventCreate(&e));
+    RA_CUDA(cudaEventRecord(h->uploaded, s));
+    RA_CUDA(cudaStreamWaitEvent(h->stream, h->uploaded, 0));
     // the caller may free its buffers on return
-    RA_CUDA(cudaStreamSynchronize(s));
+    RA_CUDA(cudaEventSynchronize(h->uploaded));
     return RA_OK;
 }
 
@@ -458,7 +531,9 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
             return RA_EDEVICE;
         }
     }
-    if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->upload, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->uploaded, cudaEventDisableTiming) != cudaSuccess) {
         delete h;
         return RA_EDEVICE;
     }
@@ -719,6 +794,8 @@ extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
         return RA_EINVAL;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
+    if (h->upload)
+        cudaStreamSynchronize(h->upload);
     serve_destroy(h);
     for (auto &tk : h->tickets)
         if (tk.second.done)
@@ -733,6 +810,10 @@ extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
     }
     if (h->fork)
         cudaEventDestroy(h->fork);
+    if (h->uploaded)
+        cudaEventDestroy(h->uploaded);
+    if (h->upload)
+        cudaStreamDestroy(h->upload);
     delete h;
     return RA_OK;
 }

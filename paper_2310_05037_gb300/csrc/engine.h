@@ -239,6 +239,8 @@ struct rawalign_dtw {
     rawalign_dtw_config_t cfg{};
     cudaStream_t stream = nullptr;
     cudaStream_t aux[kMaxClasses] = {};   // one graph branch per launch class
+    cudaStream_t upload = nullptr;         // batch uploads: overlap the previous batch's kernels
+    cudaEvent_t uploaded = nullptr;
     cudaEvent_t fork = nullptr, join[kMaxClasses] = {};
     int device = 0;
     int sm_count = 152;
@@ -375,17 +377,34 @@ inline void shorten_longest(std::vector<PlanItem> &items, int sm_count, const do
 // kMaxClasses would be needed.
 inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &order, std::vector<ClassLaunch> &classes)
 {
+    // counting sort by (variant, ring size, longest first in quarter-octave
+    // steps of the cost): linear in the number of items and stable, so the
+    // order is deterministic
     const size_t n = items.size();
+    constexpr int kCaps = 8, kCostBins = 256;
+    auto cap_index = [](int cap) {
+        int i = 0;
+        while (i < kCaps - 1 && (128 << (2 * i)) < cap)
+            ++i;
+        return i;
+    };
+    auto key = [&](const PlanItem &it) {
+        const double c = std::max(it.cost, 1.0);
+        const int bin = std::min(kCostBins - 1, (int)(std::log2(c) * 4.0));
+        return (it.variant * kCaps + cap_index(it.cap)) * kCostBins + (kCostBins - 1 - bin);
+    };
+    const int n_keys = kNumVariants * kCaps * kCostBins;
+    std::vector<uint32_t> start(n_keys + 1, 0);
+    std::vector<int> keys(n);
+    for (size_t x = 0; x < n; ++x) {
+        keys[x] = key(items[x]);
+        ++start[keys[x] + 1];
+    }
+    for (int q = 0; q < n_keys; ++q)
+        start[q + 1] += start[q];
     order.resize(n);
     for (size_t x = 0; x < n; ++x)
-        order[x] = (int)x;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (items[x].variant != items[y].variant)
-            return items[x].variant < items[y].variant;
-        if (items[x].cap != items[y].cap)
-            return items[x].cap < items[y].cap;
-        return items[x].cost > items[y].cost;
-    });
+        order[start[keys[x]]++] = (int)x;
     classes.clear();
     size_t pos = 0;
     while (pos < n) {
