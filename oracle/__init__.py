@@ -152,6 +152,9 @@ def lib():
                 C.c_int, f32, f32, pf, pu8, u64, pf, pu64, C.c_uint32,
                 C.POINTER(Candidate), C.c_uint32, pa, pu64, C.POINTER(Result), C.c_int,
             ]
+            pi32 = C.POINTER(C.c_int32)
+            L.ora_traceback_f32.restype = C.c_int
+            L.ora_traceback_f32.argtypes = [pf, i64, pf, i64, i64, i64, i64, C.c_int, pi32, pi32, i64, pi64, pf]
             L.ora_map_batch.restype = C.c_int
             L.ora_map_batch.argtypes = [
                 C.c_int, f32, f32, C.c_int, pf, pu8, u64, pf, pu64, C.c_uint32,
@@ -374,3 +377,21 @@ def map_anchored(k, b_match, score_threshold, pore, ref2bit, ref_len, events, re
     if rc != 0:
         raise ValueError("oracle rejected the batch (%d)" % rc)
     return out
+
+
+def traceback_f32(e, r, band_w=-1, num=0, den=0, end_mode=END_GLOBAL):
+    """Optimal warping path (ties: NW, then N, then W) from (0,0) to the end
+    cell: (cost, path as an (L, 2) int array of (i, j)); empty when no
+    in-band path reaches the end."""
+    e, r = _f32(e), _f32(r)
+    n, m = len(e), len(r)
+    cap = n + m - 1
+    pi = np.zeros(cap, np.int32)
+    pj = np.zeros(cap, np.int32)
+    ln = C.c_int64()
+    cost = C.c_float()
+    rc = lib().ora_traceback_f32(_P(e, C.c_float), n, _P(r, C.c_float), m, band_w, num, den, end_mode,
+                                 _P(pi, C.c_int32), _P(pj, C.c_int32), cap, C.byref(ln), C.byref(cost))
+    if rc != 0:
+        raise ValueError("oracle rejected the input (%d)" % rc)
+    return np.float32(cost.value), np.stack([pi[: ln.value], pj[: ln.value]], axis=1)

@@ -762,3 +762,68 @@ int ora_map_anchored(int k, float b_match, float score_threshold,
     ora_decide(n_reads, cands, n_cands, score_threshold, out, use_f64);
     return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Traceback (the warping path; the paper computes it only on request,
+ * Sec. 2.4): from the end cell, step to the predecessor whose DP value is
+ * the minimum the recurrence took, preferring NW, then N, then W on ties,
+ * until (0,0).  The path is returned from (0,0) to the end cell.  Every cell
+ * of the full FP32 table comes from ora_dtw_f32.
+ * ------------------------------------------------------------------------- */
+int ora_traceback_f32(const float *e, int64_t n, const float *r, int64_t m,
+                      int64_t band_w, int64_t num, int64_t den, int end_mode,
+                      int32_t *path_i, int32_t *path_j, int64_t cap,
+                      int64_t *path_len, float *cost)
+{
+    if (n < 1 || m < 1 || cap < n + m - 1)
+        return -1;
+    float *D = (float *)malloc(sizeof(float) * (size_t)n * (size_t)m);
+    if (!D)
+        return -2;
+    int64_t ei, ej, we;
+    uint64_t cells;
+    if (ora_dtw_f32(e, n, r, m, band_w, num, den, end_mode, cost, &ei, &ej, &cells, &we, D) != 0) {
+        free(D);
+        return -1;
+    }
+    *path_len = 0;
+    if (!(*cost < INFINITY) || ei < 0) {
+        free(D);
+        return 0;
+    }
+    int64_t i = ei, j = ej, len = 0;
+    while (1) {
+        path_i[len] = (int32_t)i;
+        path_j[len] = (int32_t)j;
+        ++len;
+        if (i == 0 && j == 0)
+            break;
+        float nw = (i > 0 && j > 0) ? D[(i - 1) * m + (j - 1)] : INFINITY;
+        float no = (i > 0) ? D[(i - 1) * m + j] : INFINITY;
+        float wv = (j > 0) ? D[i * m + (j - 1)] : INFINITY;
+        float best = nw;
+        if (no < best)
+            best = no;
+        if (wv < best)
+            best = wv;
+        if (nw == best) {
+            --i;
+            --j;
+        } else if (no == best) {
+            --i;
+        } else {
+            --j;
+        }
+    }
+    for (int64_t a = 0, b = len - 1; a < b; ++a, --b) {
+        int32_t t = path_i[a];
+        path_i[a] = path_i[b];
+        path_i[b] = t;
+        t = path_j[a];
+        path_j[a] = path_j[b];
+        path_j[b] = t;
+    }
+    *path_len = len;
+    free(D);
+    return 0;
+}

@@ -96,6 +96,10 @@ int ora_map_anchored(int k, float b_match, float score_threshold,
                      uint32_t n_reads, const ora_candidate_t *cands,
                      uint32_t n_cands, const ora_anchor_t *anchors,
                      const uint64_t *anchor_offsets, ora_result_t *out, int use_f64);
+int ora_traceback_f32(const float *e, int64_t n, const float *r, int64_t m,
+                      int64_t band_w, int64_t num, int64_t den, int end_mode,
+                      int32_t *path_i, int32_t *path_j, int64_t cap,
+                      int64_t *path_len, float *cost);
 int ora_map_batch(int k, float b_match, float score_threshold, int end_mode,
                   const float *pore, const uint8_t *ref2bit, uint64_t ref_len,
                   const float *events, const uint64_t *read_offsets,

@@ -435,3 +435,86 @@ def test_planted_anchor_mistake_is_caught():
         if wrong(e, r, anchors) != O.anchored_brute(e, r, anchors):
             diffs += 1
     assert diffs > 20
+
+
+# ---------------------------------------------------------------- traceback (optional path output)
+def _load_traceback():
+    rows = []
+    for line in open(os.path.join(GOLD, "traceback_hand_worked.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, ev, rv, bw, mode, cost, path = [x.strip() for x in line.split("|")]
+        p = [tuple(int(v) for v in c.split(",")) for c in path.split()]
+        rows.append((name, [float(x) for x in ev.split()], [float(x) for x in rv.split()], int(bw),
+                     O.END_GLOBAL if mode == "global" else O.END_FREE, float(cost), p))
+    return rows
+
+
+@pytest.mark.parametrize("case", _load_traceback(), ids=lambda c: c[0])
+def test_traceback_hand_worked(case):
+    name, e, r, bw, mode, cost, path = case
+    c, p = O.traceback_f32(e, r, bw, end_mode=mode)
+    assert float(c) == cost
+    assert [tuple(x) for x in p.tolist()] == path
+
+
+def _all_optimal_paths(e, r, band, end_mode):
+    """Every path from (0,0) (N/W/NW steps, in band) ending in the last row
+    (FREE) or at the corner (GLOBAL), with its FP64 cost; the optimal ones."""
+    n, m = len(e), len(r)
+    out = []
+
+    def walk(i, j, acc, path):
+        if i == n - 1 and (end_mode == O.END_FREE or j == m - 1):
+            out.append((acc, list(path)))
+        for di, dj in ((0, 1), (1, 0), (1, 1)):
+            a, b = i + di, j + dj
+            if a < n and b < m and O.in_band(band, a, b):
+                path.append((a, b))
+                walk(a, b, acc + abs(float(e[a]) - float(r[b])), path)
+                path.pop()
+
+    if O.in_band(band, 0, 0):
+        walk(0, 0, abs(float(e[0]) - float(r[0])), [(0, 0)])
+    if not out:
+        return np.inf, []
+    best = min(a for a, _ in out)
+    return best, [p for a, p in out if a == best]
+
+
+def test_traceback_is_an_optimal_path_and_resums_to_the_cost():
+    """On small integer tables (exact sums) the returned path is one of the
+    optimal warping paths found by enumeration; on random FP32 tables the
+    path's cells, summed in path order in FP32, give the cost bit for bit."""
+    rng = np.random.default_rng(33)
+    for it in range(600):
+        n, m = int(rng.integers(1, 7)), int(rng.integers(1, 7))
+        if it % 2:
+            e = rng.integers(-3, 4, size=n).astype(np.float32)
+            r = rng.integers(-3, 4, size=m).astype(np.float32)
+        else:
+            e = rng.standard_normal(n).astype(np.float32)
+            r = rng.standard_normal(m).astype(np.float32)
+        bw = int(rng.integers(-1, 3))
+        mode = int(rng.integers(0, 2))
+        cost, path = O.traceback_f32(e, r, bw, end_mode=mode)
+        band = O.band_params(n, m, bw)
+        if not np.isfinite(cost):
+            assert len(path) == 0
+            continue
+        assert tuple(path[0]) == (0, 0) and path[-1][0] == n - 1
+        if mode == O.END_GLOBAL:
+            assert path[-1][1] == m - 1
+        steps = np.diff(path, axis=0)
+        assert all(tuple(s) in ((0, 1), (1, 0), (1, 1)) for s in steps)
+        assert all(O.in_band(band, int(i), int(j)) for i, j in path)
+        s = np.float32(0)
+        for k, (i, j) in enumerate(path):
+            d = np.float32(abs(np.float32(e[i] - r[j])))
+            s = d if k == 0 else np.float32(d + s)
+        assert s == cost
+        if it % 2:
+            best, opt = _all_optimal_paths(e, r, band, mode)
+            assert float(cost) == best
+            assert [tuple(x) for x in path.tolist()] in [[tuple(c) for c in p] for p in opt]
