@@ -260,6 +260,24 @@ int rawalign_dtw_submit_anchored(rawalign_dtw_t *h, const float *events, const u
                                  const rawalign_anchor_t *anchors, const uint64_t *anchor_offsets,
                                  uint64_t *ticket);
 
+/* The optimal warping path of one alignment (the paper maps with the score
+ * alone and writes the path only on request, Sec. 2.4).  events: the read's
+ * n_events events (host); cand: one candidate (its read_id is only copied to
+ * the result); end_mode: RA_END_GLOBAL or RA_END_FREE.  The DP is the same as
+ * the batch kernels' (bit-identical cost); the path steps back from the end
+ * cell to the neighbour that held the minimum, NW first, then N, then W on
+ * ties.  path_i / path_j (host, cap >= n_events + m - 1 entries) receive the
+ * path from (0,0) to the end cell, *path_len its length (0 when no in-band
+ * path reaches the end); result receives cost, score, end, w_eff and cells
+ * (is_best = 0, decision = RA_UNMAPPED: one candidate decides nothing).  The
+ * call runs on the handle's stream and returns when done.  It takes from the
+ * arena, until it returns, about 1 byte per in-band cell plus 30 bytes per
+ * event and 12 per column.  Errors: RA_EINVAL (bad arguments, cap too small,
+ * non-finite events), RA_ENOMEM (arena too small), RA_EDEVICE. */
+int rawalign_dtw_traceback(rawalign_dtw_t *h, const float *events, uint32_t n_events,
+                           const rawalign_candidate_t *cand, int32_t end_mode, int32_t *path_i,
+                           int32_t *path_j, uint32_t cap, uint32_t *path_len, rawalign_result_t *result);
+
 /* Bytes of arena a batch of this shape needs (planning aid for callers).
  * Not included: ring scratch for alignments whose band is too wide for the
  * shared-memory ring (about 2w+1 > 2000 columns).  Those take it from the

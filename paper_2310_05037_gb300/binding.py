@@ -116,6 +116,8 @@ SIGNATURES = {
                                                 C.c_uint32, C.c_void_p, C.c_void_p, _u64p]),
     "rawalign_dtw_submit_anchored": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
                                                C.c_uint32, C.c_void_p, C.c_void_p, _u64p]),
+    "rawalign_dtw_traceback": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_int32, C.c_void_p,
+                                         C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.c_void_p]),
     "rawalign_dtw_run_batch": (C.c_int, [C.c_void_p, C.c_uint64, _u64p]),
     "rawalign_dtw_release_batch": (C.c_int, [C.c_void_p, C.c_uint64]),
     "rawalign_dtw_destroy": (C.c_int, [C.c_void_p]),
@@ -217,6 +219,23 @@ def rawalign_dtw_submit_anchored(h, events, read_offsets, cands, anchors, anchor
         h, _ptr(ev), _ptr(offs), len(offs) - 1, _ptr(cands), len(cands), _ptr(a) if len(a) else None, _ptr(aoffs),
         C.byref(t)))
     return t.value
+
+
+def rawalign_dtw_traceback(h, events, cand, end_mode=RA_END_GLOBAL, k=6):
+    """(result record, path as an (L, 2) int32 array of (i, j) from (0,0))."""
+    ev = np.ascontiguousarray(events, np.float32)
+    cd = np.ascontiguousarray(np.asarray(cand).reshape(1))
+    if cd.dtype != CANDIDATE_DTYPE:
+        raise TypeError("the candidate must use CANDIDATE_DTYPE")
+    m = int(cd["ref_len_bases"][0]) - k + 1
+    cap = max(len(ev) + max(m, 1) - 1, 1)
+    pi = np.zeros(cap, np.int32)
+    pj = np.zeros(cap, np.int32)
+    ln = C.c_uint32()
+    res = np.zeros(1, RESULT_DTYPE)
+    _check("rawalign_dtw_traceback", load().rawalign_dtw_traceback(
+        h, _ptr(ev), len(ev), _ptr(cd), int(end_mode), _ptr(pi), _ptr(pj), cap, C.byref(ln), _ptr(res)))
+    return res[0], np.stack([pi[: ln.value], pj[: ln.value]], axis=1)
 
 
 def rawalign_dtw_run_batch(h, batch: int) -> int:
@@ -333,6 +352,9 @@ class Aligner:
 
     def prepare_anchored(self, events, read_offsets, cands, anchors, anchor_offsets):
         return rawalign_dtw_prepare_anchored(self.h, events, read_offsets, cands, anchors, anchor_offsets)
+
+    def traceback(self, events, cand, end_mode=RA_END_GLOBAL):
+        return rawalign_dtw_traceback(self.h, events, cand, end_mode, k=self.cfg.k)
 
     def run(self, batch):
         return rawalign_dtw_run_batch(self.h, batch)
