@@ -391,8 +391,13 @@ def main():
         closed = loop.run(max_chunks=args.serve_chunks, in_flight=512).summary()
         rt = ServingLoop(als, sreads[::-1]).run(max_chunks=10 ** 9, in_flight=512, realtime=True, chunk_s=0.4,
                                                  duration_s=args.serve_realtime_s, arrival_rate=1280.0).summary()
+        from paper_2310_05037_gb300.serving import collect_trajectories, decision_study
+
+        trs = collect_trajectories(als, sreads[:512], chunk=180, max_events=4000, in_flight=512)
+        study = decision_study(trs, [10.0, 20.0, 30.0, 40.0, 60.0], max_events=4000)
         als.close()
         out["served"] = {"closed_loop": closed, "realtime": rt,
+                         "decision_study": {"reads": len(trs), "by_threshold": study},
                          "workload": "Read-Until serving: Poisson stream, 512 reads in flight, 180-event chunks, "
                                      "<= 4000 events, 1-32 candidates, band 64, FREE end, 50% off-target reads"}
         out["speedup_served_vs_plain"] = (round(closed["gcups"] / out["plain_kernel"]["gcups"], 1)

@@ -170,3 +170,112 @@ class ServingLoop:
                 B.rawalign_dtw_flush(self.al.h)
                 B.rawalign_dtw_poll(self.al.h, t, 0, timeout_us=-1)
         return st
+
+
+@dataclasses.dataclass
+class Trajectory:
+    """One read's results after each chunk: events aligned so far, the best
+    candidate's score and index, and the smallest cost over its candidates."""
+    read_id: int
+    on_target: bool
+    true_cand: int
+    events: list = dataclasses.field(default_factory=list)
+    best_score: list = dataclasses.field(default_factory=list)
+    best_cand: list = dataclasses.field(default_factory=list)
+    min_cost: list = dataclasses.field(default_factory=list)
+    mapped: list = dataclasses.field(default_factory=list)  # the library's decision at its own threshold
+
+
+def collect_trajectories(aligner, reads, chunk=180, max_events=4000, in_flight=512):
+    """Feeds every read chunk by chunk up to max_events (or its end) through
+    submit_chunk / flush / poll, keeping in_flight reads admitted, and
+    records each read's trajectory.  Reads are not stopped early, so every
+    threshold can be studied on the same trajectories."""
+    pending = list(reads)
+    live = {}
+    out = {}
+    while pending or live:
+        while pending and len(live) < in_flight:
+            rd = pending[0]
+            q = min(chunk, len(rd.events), max_events)
+            last = q >= min(max_events, len(rd.events))
+            try:
+                t = B.rawalign_dtw_submit_chunk(aligner.h, rd.read_id, rd.events[:q], rd.cands, last)
+            except B.RawAlignError as e:
+                if e.code == B.RA_EAGAIN:
+                    break
+                raise
+            pending.pop(0)
+            live[rd.read_id] = [rd, q, t]
+            out[rd.read_id] = Trajectory(rd.read_id, rd.on_target, getattr(rd, "true_cand", -1))
+        B.rawalign_dtw_flush(aligner.h)
+        done = []
+        for rid, st in live.items():
+            rd, q, t = st
+            res = B.rawalign_dtw_poll(aligner.h, t, 64, timeout_us=-1)
+            tr = out[rid]
+            sc = res["score"].astype(np.float64)
+            b = int(np.argmax(sc)) if len(sc) else -1
+            tr.events.append(q)
+            tr.best_score.append(float(sc[b]) if b >= 0 else -np.inf)
+            tr.best_cand.append(b)
+            tr.min_cost.append(float(res["cost"].min()) if len(res) else np.inf)
+            tr.mapped.append(bool(len(res) and np.any(res["decision"] == B.RA_MAPPED)))
+            end = min(max_events, len(rd.events))
+            if q >= end:
+                done.append(rid)
+                continue
+            q2 = min(q + chunk, end)
+            st[1] = q2
+            st[2] = B.rawalign_dtw_submit_chunk(aligner.h, rid, rd.events[q:q2], None, q2 >= end)
+        for rid in done:
+            live.pop(rid)
+    return [out[rd.read_id] for rd in reads if rd.read_id in out]
+
+
+def decision_study(trajectories, thresholds, b_match=0.4, max_events=4000):
+    """Read-Until decision policy (Sec. 1, Sec. 3.1) replayed on recorded
+    trajectories for several Score_Threshold values.  After each chunk a read
+    is accepted when its best score reaches the threshold, rejected when no
+    candidate can reach it any more even if every remaining event matched
+    exactly (B_Match * max_events - smallest cost < threshold; costs only
+    grow), else it continues; at max_events it is undecided.  Per threshold:
+    counts, the share of accepted reads whose best candidate is the true
+    locus (precision), the share of on-target reads accepted at their true
+    locus (recall), and the events consumed before the decision."""
+    out = {}
+    for thr in thresholds:
+        acc = rej = und = tp = 0
+        ev_acc, ev_rej, ev_all = [], [], []
+        on_total = sum(tr.on_target for tr in trajectories)
+        for tr in trajectories:
+            decided = None
+            for k, n_ev in enumerate(tr.events):
+                if tr.best_score[k] >= thr:
+                    decided = ("accept", n_ev, tr.best_cand[k])
+                    break
+                if b_match * max_events - tr.min_cost[k] < thr:
+                    decided = ("reject", n_ev, -1)
+                    break
+            if decided is None:
+                und += 1
+                ev_all.append(tr.events[-1] if tr.events else 0)
+                continue
+            kind, n_ev, cand = decided
+            ev_all.append(n_ev)
+            if kind == "accept":
+                acc += 1
+                ev_acc.append(n_ev)
+                tp += int(tr.on_target and cand == tr.true_cand)
+            else:
+                rej += 1
+                ev_rej.append(n_ev)
+        out[float(thr)] = {
+            "accepted": acc, "rejected": rej, "undecided": und,
+            "precision": round(tp / acc, 4) if acc else None,
+            "recall": round(tp / on_total, 4) if on_total else None,
+            "mean_events_to_accept": round(float(np.mean(ev_acc)), 1) if ev_acc else None,
+            "mean_events_to_reject": round(float(np.mean(ev_rej)), 1) if ev_rej else None,
+            "median_events_to_decision": float(np.median(ev_all)) if ev_all else None,
+        }
+    return out

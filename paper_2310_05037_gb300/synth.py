@@ -452,6 +452,7 @@ class ServingRead:
     cands: np.ndarray           # CANDIDATE_DTYPE rows (read_id field = read_id)
     on_target: bool
     arrival_s: float
+    true_cand: int = -1         # index of the true locus among cands (-1: off-target)
 
 
 def config_serving(seed: int = 0x5EED0004, n_reads: int = 2048, ref_len: int = 100_000_000,
@@ -486,7 +487,7 @@ def config_serving(seed: int = 0x5EED0004, n_reads: int = 2048, ref_len: int = 1
         for s in range(nc):
             off = loc if (on and s == true_slot) else int(rng.integers(0, ref_len - span))
             c[s] = (q, off, span, 0, 0, band, 0, 1000, 1045)
-        out.append(ServingRead(q, ev, c, on, t))
+        out.append(ServingRead(q, ev, c, on, t, true_cand=true_slot if on else -1))
     return pore, ref, ref_len, out
 
 

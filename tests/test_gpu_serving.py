@@ -200,3 +200,31 @@ def test_request_loop_closed_and_realtime():
         assert rt.chunks > 0
     finally:
         al.close()
+
+
+def test_decision_policy_study():
+    """Read-Until decision policy replayed over thresholds: accepting at the
+    handle's own threshold happens exactly where the library first says
+    MAPPED; accepted counts never grow and rejected counts never shrink as
+    the threshold rises; at Score_Threshold = 20 accepted reads map to their
+    true locus."""
+    from paper_2310_05037_gb300.serving import collect_trajectories, decision_study
+
+    pore, ref, ref_len, reads = _serving_inputs(n_reads=24, max_events=900, seed=17)
+    al = _aligner(pore, ref, ref_len, slots=24, max_events=900)
+    try:
+        trs = collect_trajectories(al, reads, chunk=180, max_events=900, in_flight=24)
+    finally:
+        al.close()
+    assert len(trs) == len(reads)
+    for tr in trs:
+        k_lib = next((k for k, f in enumerate(tr.mapped) if f), None)
+        k_thr = next((k for k, sc in enumerate(tr.best_score) if sc >= np.float32(20.0)), None)
+        assert k_lib == k_thr
+    thresholds = [5.0, 10.0, 20.0, 40.0, 80.0]
+    st = decision_study(trs, thresholds, max_events=900)
+    acc = [st[t]["accepted"] for t in thresholds]
+    rej = [st[t]["rejected"] for t in thresholds]
+    assert acc == sorted(acc, reverse=True) and rej == sorted(rej)
+    assert all(st[t]["accepted"] + st[t]["rejected"] + st[t]["undecided"] == len(reads) for t in thresholds)
+    assert st[20.0]["accepted"] > 0 and st[20.0]["precision"] >= 0.9
