@@ -42,6 +42,10 @@ WORKLOADS = {
                   "FP32 global DTW"),
     "longread": ("longread_banded: 2000 reads of 20k-100k events (uniform), 2 candidates each on a 100 Mb "
                  "reference, band 5% of span, 5% skips + 5% stays, noise sd 0.4, FP32 global DTW"),
+    "batched_et": ("batched_uneven_early_termination: the batched-uneven workload (%d reads) with each read's "
+                   "true locus first among its candidates (as chaining-score order puts it) and branch-and-bound "
+                   "early termination on: the others stop once they cannot beat the read's best score; GCUPS "
+                   "counts the cells computed"),
     "anchored": ("anchored_batched: the batched-uneven shapes (20000 reads, 1-8 candidates, band 10% of span) "
                  "with anchor-guided alignment: each candidate's chain (true locus: runs of one event per k-mer "
                  "from the simulated read, 8-16 events; decoys: 0-6 random anchors), gaps aligned by banded DTW"),
@@ -186,13 +190,13 @@ def cpu_baseline(w, seconds=15.0, seed=1):
 
 def workload_name(args):
     d = WORKLOADS[args.workload]
-    return d % args.reads if args.workload == "batched" else d
+    return d % args.reads if args.workload in ("batched", "batched_et") else d
 
 
 def make_workload(S, args, rank):
     """The step's batch; every rank draws its own (weak scaling, replicas)."""
-    if args.workload == "batched":
-        return S.config_batched(n_reads=args.reads, seed=0x5EED0002 + rank)
+    if args.workload in ("batched", "batched_et"):
+        return S.config_batched(n_reads=args.reads, seed=0x5EED0002 + rank, true_first=args.workload == "batched_et")
     return S.scaled(args.workload, "full", seed=None if rank == 0 else 0x5EED1000 + rank)
 
 
@@ -234,7 +238,8 @@ def main():
     arena = 3 * need + len(w.ref2bit) + (256 << 20)  # the prepared batch and two submissions in flight
     if w.anchor_offsets is not None:  # per-gap work items and results, pieces
         arena += 3 * (len(w.anchors) + w.n_cands) * 512
-    al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena, device="cuda:%d" % local)
+    al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena, device="cuda:%d" % local,
+                   early_termination=args.workload == "batched_et")
     stream = al.stream
     anchored = w.anchor_offsets is not None
     if anchored:
@@ -251,6 +256,7 @@ def main():
         t = one_step()
         res = al.poll(t, w.n_cands)
     cells_step = int(res["cells"].sum())
+    pruned_step = int(np.sum(res["status"] == B.RA_RESULT_PRUNED))
     reads_step = w.n_reads
     launches_step = al.stats(batch).launches
 
@@ -306,6 +312,7 @@ def main():
                          "between timed steps" % (m_total * 4 / 1e6, len(w.events) * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "reads_per_s": round(sum_over_ranks(reads_step * args.steps, world) / total_s, 1),
+        "pruned_alignments_per_step": pruned_step,
         "dtw_kernel_ms": round(dtw_avg_ms, 3),
         "gpu_launches": int(launches_step * args.steps),
         "roofline": roofline, "clocks": clocks,

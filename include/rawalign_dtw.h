@@ -58,6 +58,10 @@ typedef enum {
 
 enum { RA_END_GLOBAL = 0, RA_END_FREE = 1 };            /* end of the DTW */
 enum { RA_UNMAPPED = 0, RA_MAPPED = 1, RA_PENDING = 2 };/* decision */
+/* result.status besides RA_OK: the candidate was stopped by early
+ * termination (config.early_termination); cost then holds a lower bound of
+ * its cost, score the matching upper bound of its score, end = (-1,-1). */
+enum { RA_RESULT_PRUNED = 1 };
 /* kernel choice: AUTO picks a striped variant per alignment; PLAIN runs one
  * alignment per launch; RA_KERNEL_VARIANT0 + v forces striped variant v for
  * every alignment (tuning and tests): v = 0..9 are (lanes per alignment, rows
@@ -78,6 +82,8 @@ typedef struct {
     int32_t serve_slots;       /* serving: reads admitted at once (0 = none) */
     int32_t serve_max_events;  /* serving: events per read at most */
     const char *autotune_path; /* optional tuning table written by the tuner */
+    int32_t early_termination; /* 1: branch and bound in GLOBAL batches (Sec. 2.4.1), see prepare_batch */
+    int32_t pad;
 } rawalign_dtw_config_t;
 
 /* One candidate region of the reference for one read (48 bytes). */
@@ -168,7 +174,18 @@ int rawalign_dtw_poll(rawalign_dtw_t *h, uint64_t ticket, rawalign_result_t *out
 /* Device-resident batches for repeated runs (the timing harness): prepare
  * copies the inputs into the arena and plans the work once; run re-executes
  * every step of the path on the resident inputs (as one CUDA graph) and
- * returns a ticket; release frees the batch. */
+ * returns a ticket; release frees the batch.
+ *
+ * Early termination (config.early_termination = 1; batches with GLOBAL end,
+ * not anchor-guided; Sec. 2.4.1): the first candidate of each read, in the
+ * order given (callers sort candidates by chaining score, as the paper
+ * does), runs in a first wave; the others run in a second wave and stop
+ * after any stripe (a block of rows) whose last row shows that even the
+ * smallest cost still reachable cannot beat the read's best score found so
+ * far.  Stopped candidates come back with status RA_RESULT_PRUNED.  The
+ * read's best candidate, its result and the read's decision are the same as
+ * without early termination; which other candidates are stopped, and their
+ * bounds, may vary from run to run.  Unstopped results are unchanged. */
 int rawalign_dtw_prepare_batch(rawalign_dtw_t *h, const float *events, const uint64_t *read_offsets,
                                uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
                                uint64_t *batch);

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "librawalign_dtw.so")
 RA_OK, RA_EINVAL, RA_ENOMEM, RA_EAGAIN, RA_ENOTREADY, RA_ETIMEDOUT, RA_EDEVICE, RA_ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7
 RA_END_GLOBAL, RA_END_FREE = 0, 1
 RA_UNMAPPED, RA_MAPPED, RA_PENDING = 0, 1, 2
+RA_RESULT_PRUNED = 1
 RA_KERNEL_AUTO, RA_KERNEL_PLAIN = 0, 1
 RA_KERNEL_VARIANT0 = 16
 VARIANTS = [(32, 16), (16, 16), (32, 8), (16, 8), (8, 8), (4, 8), (16, 24), (8, 24), (32, 24), (4, 24)]
@@ -49,6 +50,8 @@ class Config(C.Structure):
         ("serve_slots", C.c_int32),
         ("serve_max_events", C.c_int32),
         ("autotune_path", C.c_char_p),
+        ("early_termination", C.c_int32),
+        ("pad", C.c_int32),
     ]
 
 
@@ -314,7 +317,8 @@ class Aligner:
 
     def __init__(self, pore, ref2bit, ref_len, arena_bytes=1 << 30, k=6, b_match=0.4, score_threshold=20.0,
                  end_mode=RA_END_GLOBAL, kernel=RA_KERNEL_AUTO, stream=None, serve_slots=0,
-                 serve_max_events=0, max_candidates=64, device="cuda:0", autotune_path=None):
+                 serve_max_events=0, max_candidates=64, device="cuda:0", autotune_path=None,
+                 early_termination=False):
         import torch
 
         self.torch = torch
@@ -334,6 +338,7 @@ class Aligner:
         cfg.kernel = kernel
         cfg.serve_slots = serve_slots
         cfg.serve_max_events = serve_max_events
+        cfg.early_termination = 1 if early_termination else 0
         self._tune_path = autotune_path.encode() if autotune_path else None
         cfg.autotune_path = self._tune_path
         self.cfg = cfg

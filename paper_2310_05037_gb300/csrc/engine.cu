@@ -99,6 +99,8 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     std::vector<CombineDesc> cdesc(b.anchored ? n_cands : 0);
     // pass 1 (sequential, cheap): candidate checks and each candidate's row
     // of expected values in the packed r array
+    b.et = h->cfg.early_termination && !b.anchored && !b.plain && h->cfg.end_mode == RA_END_GLOBAL;
+    std::vector<uint32_t> first_of_read(b.et ? n_reads : 0, UINT32_MAX);
     uint64_t r_total = 0;
     for (uint32_t c = 0; c < n_cands; ++c) {
         const rawalign_candidate_t &cd = cands[c];
@@ -114,6 +116,8 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
             return RA_EINVAL;
         if (b.anchored && anchor_offs[c + 1] < anchor_offs[c])
             return RA_EINVAL;
+        if (b.et && first_of_read[cd.read_id] == UINT32_MAX)
+            first_of_read[cd.read_id] = c;
         sig[c].ref_off = cd.ref_offset;
         sig[c].r_off = r_total;
         sig[c].len = cd.ref_len_bases;
@@ -160,6 +164,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
                 PlanItem &it = items[c];
                 fill_work(it, ev0, r0, n, m, band, wrep, (int32_t)c, (int32_t)cd.read_id, (int32_t)n);
                 schedule_item(it, band, n);
+                it.wave = (b.et && first_of_read[cd.read_id] != c) ? 1 : 0;
                 continue;
             }
             // Sec. 2.4.2: gap 0, anchor 1, gap 1, ..., anchor K, gap K in path order
@@ -377,6 +382,9 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
             int qi = 0;
             for (size_t ci = 0; ci < b.classes.size(); ++ci) {
                 auto &cl = b.classes[ci];
+                // the second wave (early termination) starts once the first has joined
+                if (ci > 0 && cl.wave != b.classes[ci - 1].wave)
+                    RA_CUDA(cudaEventRecord(h->fork, s));
                 cudaStream_t cs = h->aux[ci];
                 RA_CUDA(cudaStreamWaitEvent(cs, h->fork, 0));
                 StripeParams p{};
@@ -394,6 +402,7 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
                 p.ring_in_smem = cl.ring_in_smem;
                 p.b_match = h->cfg.b_match;
                 p.end_free = end_free;
+                p.early_term = cl.wave == 1;
                 p.err = b.d_err;
                 RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
                 ++launches;

@@ -64,6 +64,7 @@ struct StripeParams {
     float b_match;
     int end_free;                  // 1: FREE end (min over the last row)
     int *err;                      // error word (first failing work item + 1)
+    int early_term;                // 1: branch and bound against the per-read best (GLOBAL end)
 };
 
 // Anchor-guided alignment (Sec. 2.4.2): one candidate's cost is the sum, in
@@ -95,6 +96,7 @@ cudaError_t launch_check_events(const float *ev, uint64_t n, int *err, cudaStrea
 cudaError_t launch_stripe(int G, int HR, const StripeParams &p, int grid, int block, size_t smem,
                           cudaStream_t s);
 int stripe_max_blocks_per_sm(int G, int HR, int block, size_t smem);
+void *pick_stripe_et(int G, int HR, bool smem_ring);  // stripe_kernel_et.cu
 cudaError_t launch_plain(const WorkDesc *w, const float *events, const float *r_all, float *diag,
                          rawalign_result_t *results, unsigned long long *best_keys, float b_match,
                          int end_free, cudaStream_t s);

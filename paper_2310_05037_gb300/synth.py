@@ -253,10 +253,11 @@ def _lognormal_lengths(rng, n, median, sigma, lo, hi):
 
 def config_batched(seed: int = 0x5EED0002, n_reads: int = 20_000, ref_len: int = 100_000_000,
                    median: int = 1500, sigma: float = 0.6, lo: int = 200, hi: int = 8000,
-                   max_cands: int = 8, band_frac: float = 0.10) -> Workload:
+                   max_cands: int = 8, band_frac: float = 0.10, true_first: bool = False) -> Workload:
     """Batched uneven DTW: lognormal read lengths (median 1500, 200..8000),
     1..8 candidates per read (1 true + decoys), span = n * U(0.9,1.3), band
-    10 % of the span."""
+    10 % of the span.  true_first puts the true locus first among a read's
+    candidates, as sorting by chaining score would (same random draws)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     pore = pore_table(seed ^ 0xA5A5)
     ref = hashed_reference(seed, ref_len)
@@ -273,6 +274,8 @@ def config_batched(seed: int = 0x5EED0002, n_reads: int = 20_000, ref_len: int =
         reads.append(ev)
         nc = int(rng.integers(1, max_cands + 1))
         true_slot = int(rng.integers(0, nc))
+        if true_first:
+            true_slot = 0
         for c in range(nc):
             m = int(math.floor(n * rng.uniform(0.9, 1.3)))
             span = m + K - 1

@@ -66,6 +66,7 @@ int main(void) {
   O(rawalign_result_t, is_best); O(rawalign_result_t, decision);
   O(rawalign_dtw_config_t, arena_dev); O(rawalign_dtw_config_t, arena_bytes); O(rawalign_dtw_config_t, cuda_stream);
   O(rawalign_dtw_config_t, max_candidates); O(rawalign_dtw_config_t, kernel); O(rawalign_dtw_config_t, autotune_path);
+  O(rawalign_dtw_config_t, early_termination);
   return 0;
 }
 """
