@@ -179,10 +179,9 @@ int rawalign_dtw_poll(rawalign_dtw_t *h, uint64_t ticket, rawalign_result_t *out
  * Early termination (config.early_termination = 1; batches with GLOBAL end,
  * not anchor-guided; Sec. 2.4.1): the first candidate of each read, in the
  * order given (callers sort candidates by chaining score, as the paper
- * does), runs in a first wave; the others run in a second wave and stop
- * after any stripe (a block of rows) whose last row shows that even the
- * smallest cost still reachable cannot beat the read's best score found so
- * far.  Stopped candidates come back with status RA_RESULT_PRUNED.  The
+ * does), is queued ahead of the others; every candidate stops after any
+ * stripe (a block of rows) whose last row shows that even the smallest cost
+ * still reachable cannot beat the read's best score found so far.  Stopped candidates come back with status RA_RESULT_PRUNED.  The
  * read's best candidate, its result and the read's decision are the same as
  * without early termination; which other candidates are stopped, and their
  * bounds, may vary from run to run.  Unstopped results are unchanged. */

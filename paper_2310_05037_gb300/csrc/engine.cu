@@ -382,9 +382,6 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
             int qi = 0;
             for (size_t ci = 0; ci < b.classes.size(); ++ci) {
                 auto &cl = b.classes[ci];
-                // the second wave (early termination) starts once the first has joined
-                if (ci > 0 && cl.wave != b.classes[ci - 1].wave)
-                    RA_CUDA(cudaEventRecord(h->fork, s));
                 cudaStream_t cs = h->aux[ci];
                 RA_CUDA(cudaStreamWaitEvent(cs, h->fork, 0));
                 StripeParams p{};
@@ -402,7 +399,7 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
                 p.ring_in_smem = cl.ring_in_smem;
                 p.b_match = h->cfg.b_match;
                 p.end_free = end_free;
-                p.early_term = cl.wave == 1;
+                p.early_term = b.et;
                 p.err = b.d_err;
                 RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
                 ++launches;

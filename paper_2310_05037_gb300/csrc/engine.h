@@ -176,7 +176,6 @@ struct Arena {
 };
 
 struct ClassLaunch {
-    int wave = 0;              // launches of wave 1 start after every wave-0 launch has ended
     int G = 0, HR = 0;
     double max_cost = 0;       // lane-steps of the class's largest alignment
     int first = 0, count = 0;  // range in the sorted work array
@@ -205,7 +204,7 @@ struct Batch {
     int max_rows = 0;
     uint32_t n_work = 0;                    // DTW work items (candidates, or gaps when anchored)
     bool anchored = false;                  // anchor-guided batch (Sec. 2.4.2)
-    bool et = false;                        // early termination (Sec. 2.4.1): two waves
+    bool et = false;                        // early termination (Sec. 2.4.1)
     rawalign_result_t *d_pres = nullptr;    // anchored: per-gap DTW results
     unsigned long long *d_pkeys = nullptr;  // anchored: per-gap keys (unused by the decision)
     PieceRef *d_plan = nullptr;             // anchored: pieces of every candidate in path order
@@ -310,7 +309,7 @@ inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &o
 // One piece of work as planned on the host.
 struct PlanItem {
     WorkDesc wd;
-    int wave = 0;       // early termination: 0 = first candidate of its read, 1 = the others
+    int wave = 0;       // early termination: 0 = first candidate of its read (queued first), 1 = the others
     int variant = 0;
     int cap = 0;        // ring entries the piece needs (power of two)
     double cost = 0;    // lane-steps: longest first
@@ -380,9 +379,12 @@ inline void shorten_longest(std::vector<PlanItem> &items, int sm_count, const do
 // kMaxClasses would be needed.
 inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &order, std::vector<ClassLaunch> &classes)
 {
-    // counting sort by (wave, variant, ring size, longest first in
+    // counting sort by (variant, ring size, wave, longest first in
     // quarter-octave steps of the cost): linear in the number of items and
-    // stable, so the order is deterministic
+    // stable, so the order is deterministic.  With early termination each
+    // class's queue holds the reads' first candidates before the others, so
+    // that a read's best score is usually known when its other candidates
+    // reach their first bound check.
     const size_t n = items.size();
     constexpr int kCaps = 8, kCostBins = 256;
     auto cap_index = [](int cap) {
@@ -394,8 +396,7 @@ inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &o
     auto key = [&](const PlanItem &it) {
         const double c = std::max(it.cost, 1.0);
         const int bin = std::min(kCostBins - 1, (int)(std::log2(c) * 4.0));
-        return ((it.wave * kNumVariants + it.variant) * kCaps + cap_index(it.cap)) * kCostBins +
-               (kCostBins - 1 - bin);
+        return ((it.variant * kCaps + cap_index(it.cap)) * 2 + it.wave) * kCostBins + (kCostBins - 1 - bin);
     };
     const int n_keys = 2 * kNumVariants * kCaps * kCostBins;
     std::vector<uint32_t> start(n_keys + 1, 0);
@@ -414,14 +415,12 @@ inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &o
     while (pos < n) {
         const PlanItem &f = items[order[pos]];
         ClassLaunch cl;
-        cl.wave = f.wave;
         cl.G = kVariants[f.variant][0];
         cl.HR = kVariants[f.variant][1];
         cl.first = (int)pos;
         cl.ring_cap = f.cap;
         cl.max_cost = f.cost;
-        while (pos < n && items[order[pos]].wave == f.wave && items[order[pos]].variant == f.variant &&
-               items[order[pos]].cap == f.cap) {
+        while (pos < n && items[order[pos]].variant == f.variant && items[order[pos]].cap == f.cap) {
             cl.max_cost = std::max(cl.max_cost, items[order[pos]].cost);
             ++pos;
         }
@@ -430,9 +429,8 @@ inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &o
     }
     if (classes.size() > (size_t)kMaxClasses)
         return false;
-    std::stable_sort(classes.begin(), classes.end(), [](const ClassLaunch &x, const ClassLaunch &y) {
-        return x.wave != y.wave ? x.wave < y.wave : x.max_cost > y.max_cost;
-    });
+    std::stable_sort(classes.begin(), classes.end(),
+                     [](const ClassLaunch &x, const ClassLaunch &y) { return x.max_cost > y.max_cost; });
     return true;
 }
 

@@ -1,8 +1,8 @@
 """Early termination (branch and bound, Sec. 2.4.1) through the C ABI.
 
-With config.early_termination the first candidate of each read runs first
-and the others stop once their stripe-end lower bound cannot beat the read's
-best score so far.  Checked against the oracle (which computes every
+With config.early_termination the first candidate of each read is queued
+first, and any candidate stops once its stripe-end lower bound cannot beat
+the read's best score so far.  Checked against the oracle (which computes every
 candidate in full): unstopped results are bit-exact, stopped ones carry a
 cost bound <= the true cost and a score bound strictly below the read's best
 score, and every read's best candidate and decision are unchanged."""
