@@ -379,37 +379,56 @@ inline void shorten_longest(std::vector<PlanItem> &items, int sm_count, const do
 // kMaxClasses would be needed.
 inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &order, std::vector<ClassLaunch> &classes)
 {
-    // counting sort by (variant, ring size, wave, longest first in
-    // quarter-octave steps of the cost): linear in the number of items and
-    // stable, so the order is deterministic.  With early termination each
-    // class's queue holds the reads' first candidates before the others, so
-    // that a read's best score is usually known when its other candidates
-    // reach their first bound check.
+    // Launch order: counting sort by (variant, ring size, wave), then within
+    // each bucket a stable radix sort by steps, longest first.  Exact order
+    // by length matters: the groups of a warp run in lockstep until the first
+    // of them finishes, so neighbours in the queue should finish together.
+    // With early termination each bucket holds the reads' first candidates
+    // before the others.  Linear in the number of items and deterministic.
     const size_t n = items.size();
-    constexpr int kCaps = 8, kCostBins = 256;
+    constexpr int kCaps = 8;
     auto cap_index = [](int cap) {
         int i = 0;
         while (i < kCaps - 1 && (128 << (2 * i)) < cap)
             ++i;
         return i;
     };
-    auto key = [&](const PlanItem &it) {
-        const double c = std::max(it.cost, 1.0);
-        const int bin = std::min(kCostBins - 1, (int)(std::log2(c) * 4.0));
-        return ((it.variant * kCaps + cap_index(it.cap)) * 2 + it.wave) * kCostBins + (kCostBins - 1 - bin);
-    };
-    const int n_keys = 2 * kNumVariants * kCaps * kCostBins;
+    const int n_keys = kNumVariants * kCaps * 2;
     std::vector<uint32_t> start(n_keys + 1, 0);
     std::vector<int> keys(n);
     for (size_t x = 0; x < n; ++x) {
-        keys[x] = key(items[x]);
+        keys[x] = (items[x].variant * kCaps + cap_index(items[x].cap)) * 2 + items[x].wave;
         ++start[keys[x] + 1];
     }
     for (int q = 0; q < n_keys; ++q)
         start[q + 1] += start[q];
+    std::vector<uint32_t> bucket_lo(start.begin(), start.end());
     order.resize(n);
     for (size_t x = 0; x < n; ++x)
         order[start[keys[x]]++] = (int)x;
+    std::vector<int> tmp;
+    std::vector<uint32_t> cnt(1 << 16);
+    for (int q = 0; q < n_keys; ++q) {
+        const uint32_t lo = bucket_lo[q], hi = bucket_lo[q + 1];
+        if (hi - lo < 2)
+            continue;
+        tmp.resize(hi - lo);
+        auto rkey = [&](int x) { return ~(uint32_t)std::max(items[x].wd.s_end, 0); };  // ascending = longest first
+        for (int shift = 0; shift < 32; shift += 16) {
+            std::fill(cnt.begin(), cnt.end(), 0u);
+            for (uint32_t y = lo; y < hi; ++y)
+                ++cnt[(rkey(order[y]) >> shift) & 0xFFFF];
+            uint32_t acc = 0;
+            for (auto &c : cnt) {
+                const uint32_t t = c;
+                c = acc;
+                acc += t;
+            }
+            for (uint32_t y = lo; y < hi; ++y)
+                tmp[cnt[(rkey(order[y]) >> shift) & 0xFFFF]++] = order[y];
+            std::copy(tmp.begin(), tmp.end(), order.begin() + lo);
+        }
+    }
     classes.clear();
     size_t pos = 0;
     while (pos < n) {
