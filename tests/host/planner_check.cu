@@ -1,0 +1,175 @@
+// planner_check.cu -- host-only check of the batch planner (engine.h), run by
+// tests/test_host_planner.py on the CPU.  It replays the striped kernel's
+// lane schedule step by step for random alignments and every variant, and
+// verifies what the planner's closed-form period dC promises:
+//   - a lane enters each stripe at least one column before the first
+//     in-band column of its rows (its first step there is fully out of band);
+//   - every value lane 0 takes from the ring (the row above its stripe, in
+//     band) is the one the last lane of the previous stripe wrote, with the
+//     ring size ring_need() gives and the kernel's read-before-write order;
+//   - the lane holding the last row leaves it within s_end steps.
+// It also checks make_classes: classes are runs of one variant and ring
+// size, longest first inside a class (first candidates before the others),
+// classes ordered by their longest alignment.
+#include <cstdio>
+#include <random>
+
+#include "engine.h"
+
+using namespace ra_host;
+
+static int fails = 0;
+#define CHECK(c, ...)                       \
+    do {                                    \
+        if (!(c)) {                         \
+            if (fails < 20)                 \
+                printf(__VA_ARGS__);        \
+            ++fails;                        \
+        }                                   \
+    } while (0)
+
+static void check_schedule(const BandDef &band, int64_t n, int G, int HR, uint64_t &steps_checked)
+{
+    const Sched sc = schedule(band, 0, n, G, HR);
+    if (sc.s_end <= 0)
+        return;
+    const int64_t H = (int64_t)G * HR, K = (n + H - 1) / H, dC = sc.dC;
+    WorkDesc wd{};
+    wd.dC = (int32_t)dC;
+    wd.fin_wid = 0;
+    const int64_t cap = ring_need(wd, G), mask = cap - 1;
+    auto lane_rows = [&](int64_t k, int t, int64_t &r0, int64_t &r1) {
+        r0 = k * H + (int64_t)t * HR;
+        r1 = std::min(r0 + HR - 1, n - 1);
+    };
+    std::vector<int64_t> j(G), k(G, 0), b(G);
+    auto set_b = [&](int t) {
+        int64_t r0, r1;
+        lane_rows(k[t], t, r0, r1);
+        b[t] = (r0 > n - 1) ? -1 : band.hi(r1);
+    };
+    for (int t = 0; t < G; ++t) {
+        j[t] = sc.a0 - 2 - t;  // the first step computes column a0 - 1 - t
+        set_b(t);
+        int64_t r0, r1;
+        lane_rows(0, t, r0, r1);
+        if (r0 <= n - 1)
+            CHECK(j[t] + 1 < band.lo(r0), "start not out of band: G%d HR%d t%d\n", G, HR, t);
+    }
+    std::vector<std::pair<int64_t, int64_t>> tag(cap, {-9, 0});  // (stripe, column) last written
+    std::pair<int64_t, int64_t> prefetched{-9, 0};
+    const int t_last = (int)((n - 1 - (K - 1) * H) / HR);
+    int64_t holder_done = -1;
+    for (int64_t s = 0; s < sc.s_end; ++s) {
+        bool moved0 = false;
+        for (int t = 0; t < G; ++t) {
+            ++j[t];
+            if (j[t] > b[t]) {
+                if (k[t] == K - 1 && t == t_last && holder_done < 0)
+                    holder_done = s;
+                ++k[t];
+                if (k[t] < K) {
+                    j[t] -= dC;
+                    set_b(t);
+                    int64_t r0, r1;
+                    lane_rows(k[t], t, r0, r1);
+                    if (r0 <= n - 1)
+                        CHECK(j[t] < band.lo(r0), "late entry: G%d HR%d n%lld k%lld t%d j%lld lo%lld\n", G, HR,
+                              (long long)n, (long long)k[t], t, (long long)j[t], (long long)band.lo(r0));
+                } else {
+                    b[t] = INT64_MAX;
+                }
+                if (t == 0)
+                    moved0 = true;
+            }
+        }
+        // lane 0's value for its column: re-read this step after a stripe
+        // change, else prefetched last step (both before this step's store)
+        const std::pair<int64_t, int64_t> got = moved0 ? tag[j[0] & mask] : prefetched;
+        if (k[0] >= 1 && k[0] < K) {
+            const int64_t above = k[0] * H - 1, c = j[0];
+            if (c >= band.lo(above) && c <= band.hi(above))
+                CHECK(got.first == k[0] - 1 && got.second == c,
+                      "ring: G%d HR%d n%lld stripe %lld column %lld got (%lld,%lld) cap %lld dC %lld\n", G, HR,
+                      (long long)n, (long long)k[0], (long long)c, (long long)got.first, (long long)got.second,
+                      (long long)cap, (long long)dC);
+        }
+        prefetched = tag[(j[0] + 1) & mask];
+        const int w = G - 1;
+        if (k[w] < K - 1)
+            tag[j[w] & mask] = {k[w], j[w]};
+        ++steps_checked;
+    }
+    CHECK(holder_done >= 0 && holder_done < sc.s_end, "holder not done: G%d HR%d n%lld\n", G, HR, (long long)n);
+}
+
+int main()
+{
+    std::mt19937_64 rng(20240531);
+    uint64_t steps = 0, cases = 0;
+    for (int rep = 0; rep < 600; ++rep) {
+        const int64_t n = 1 + (int64_t)(rng() % (rep < 300 ? 200 : 2500));
+        const int64_t m = std::max<int64_t>(1, (int64_t)(n * (0.5 + (rng() % 1000) / 1000.0)) + (int64_t)(rng() % 7));
+        const int kind = (int)(rng() % 4);
+        int32_t band_w = kind == 0 ? -1 : (int32_t)(rng() % std::max<int64_t>(2, m / (kind == 1 ? 2 : 8)));
+        int64_t num = 0, den = 0;
+        if (kind == 3) {
+            num = 1 + (int64_t)(rng() % 9);
+            den = 1 + (int64_t)(rng() % 9);
+        }
+        BandDef band;
+        int32_t wrep;
+        if (band_for(n, m, band_w, num, den, band, wrep) != 0)
+            continue;
+        for (int v = 0; v < kNumVariants; ++v) {
+            check_schedule(band, n, kVariants[v][0], kVariants[v][1], steps);
+            ++cases;
+        }
+    }
+    // launch classes
+    for (int rep = 0; rep < 50; ++rep) {
+        std::vector<PlanItem> items(1 + rng() % 5000);
+        for (auto &it : items) {
+            it.variant = (int)(rng() % kNumVariants);
+            it.cap = 128 << (2 * (int)(rng() % 4));
+            it.wave = (int)(rng() % 2);
+            it.wd.s_end = (int32_t)(1 + rng() % 200000);
+            it.cost = (double)it.wd.s_end * kVariants[it.variant][0];
+        }
+        std::vector<int> order;
+        std::vector<ClassLaunch> cls;
+        if (!make_classes(items, order, cls)) {
+            CHECK(false, "make_classes refused\n");
+            continue;
+        }
+        std::vector<int> seen(items.size(), 0);
+        for (int x : order)
+            seen[x]++;
+        for (int c : seen)
+            CHECK(c == 1, "order is not a permutation\n");
+        size_t covered = 0;
+        for (size_t ci = 0; ci < cls.size(); ++ci) {
+            const ClassLaunch &cl = cls[ci];
+            covered += cl.count;
+            double mx = 0;
+            for (int p = cl.first; p < cl.first + cl.count; ++p) {
+                const PlanItem &it = items[order[p]];
+                CHECK(kVariants[it.variant][0] == cl.G && kVariants[it.variant][1] == cl.HR && it.cap == cl.ring_cap,
+                      "class mixes variants or rings\n");
+                mx = std::max(mx, it.cost);
+                if (p > cl.first) {
+                    const PlanItem &pv = items[order[p - 1]];
+                    CHECK(pv.wave < it.wave || (pv.wave == it.wave && pv.wd.s_end >= it.wd.s_end) ||
+                              (pv.wave > it.wave && false),
+                          "class order: wave %d/%d steps %d/%d\n", pv.wave, it.wave, pv.wd.s_end, it.wd.s_end);
+                }
+            }
+            CHECK(mx == cl.max_cost, "max cost\n");
+            if (ci > 0)
+                CHECK(cls[ci - 1].max_cost >= cl.max_cost, "classes not longest first\n");
+        }
+        CHECK(covered == items.size(), "classes do not cover the items\n");
+    }
+    printf("cases %llu steps %llu fails %d\n", (unsigned long long)cases, (unsigned long long)steps, fails);
+    return fails ? 1 : 0;
+}
