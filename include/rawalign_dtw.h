@@ -19,10 +19,11 @@
  *   - Device memory: the library places everything in the caller's arena
  *     (config.arena_dev, arena_bytes), a block of device memory the caller
  *     owns and keeps alive until rawalign_dtw_destroy returns.  The library
- *     itself calls no cudaMalloc for device memory.  Serving keeps a small
- *     pool of pinned host staging buffers (cudaHostAlloc) for its copies; the
- *     batch calls copy from and to the caller's buffers directly.  Result
- *     buffers belong to the caller.
+ *     itself calls no cudaMalloc for device memory.  On the host it keeps
+ *     pinned staging memory (cudaHostAlloc): a pool for serving's copies and
+ *     one buffer, grown on demand, for each batch's planned records; events
+ *     and results are copied from and to the caller's buffers directly.
+ *     Result buffers belong to the caller.
  *   - All work runs on config.cuda_stream (a cudaStream_t; NULL = the legacy
  *     default stream) on the device current at create time.
  *   - One handle is not thread-safe: the caller serialises calls on it.

@@ -262,23 +262,34 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     if (b.anchored) {
         if (n_plan >= (1ull << 32) || n_items >= (1ull << 31))
             return RA_EINVAL;
-        items.reserve(n_items);
-        plan.reserve(n_plan);
-        for (auto &pt_ : parts) {
-            const uint32_t ibase = (uint32_t)items.size(), pbase = (uint32_t)plan.size();
-            for (auto &it : pt_.items) {
-                it.wd.cand += (int32_t)ibase;
-                it.wd.read += (int32_t)ibase;
-                items.push_back(it);
-            }
-            for (auto pr : pt_.plan) {
-                if (pr.kind == 0)
-                    pr.idx += ibase;
-                plan.push_back(pr);
-            }
-            for (uint32_t c = pt_.c0; c < pt_.c1; ++c)
-                cdesc[c].first += pbase;
+        items.resize(n_items);
+        plan.resize(n_plan);
+        std::vector<uint64_t> ibase(parts.size() + 1, 0), pbase(parts.size() + 1, 0);
+        for (size_t t = 0; t < parts.size(); ++t) {
+            ibase[t + 1] = ibase[t] + parts[t].items.size();
+            pbase[t + 1] = pbase[t] + parts[t].plan.size();
         }
+        // each part moves its items and pieces into place in parallel
+        parallel_for(parts.size(), [&](uint64_t t0, uint64_t t1) {
+            for (uint64_t t = t0; t < t1; ++t) {
+                Part &pt_ = parts[t];
+                const uint32_t ib = (uint32_t)ibase[t], pb = (uint32_t)pbase[t];
+                for (size_t x = 0; x < pt_.items.size(); ++x) {
+                    PlanItem &it = items[ib + x];
+                    it = pt_.items[x];
+                    it.wd.cand += (int32_t)ib;
+                    it.wd.read += (int32_t)ib;
+                }
+                for (size_t x = 0; x < pt_.plan.size(); ++x) {
+                    PieceRef pr = pt_.plan[x];
+                    if (pr.kind == 0)
+                        pr.idx += ib;
+                    plan[pb + x] = pr;
+                }
+                for (uint32_t c = pt_.c0; c < pt_.c1; ++c)
+                    cdesc[c].first += pb;
+            }
+        }, 1);
     }
     b.n_work = (uint32_t)items.size();
     if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO)
@@ -293,12 +304,42 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         return RA_EINVAL;
     if (b.plain)
         b.classes.clear();
-    std::vector<WorkDesc> work(b.n_work);
-    for (uint32_t x = 0; x < b.n_work; ++x)
-        work[x] = items[order[x]].wd;
-    std::vector<int> read_of(n_cands);
-    for (uint32_t c = 0; c < n_cands; ++c)
-        read_of[c] = (int)cands[c].read_id;
+    // planned records go through a pinned staging buffer: one fast copy each
+    auto al256 = [](uint64_t x) { return (x + 255) & ~255ull; };
+    const uint64_t o_work = 0, o_sig = al256(o_work + sizeof(WorkDesc) * (uint64_t)b.n_work);
+    const uint64_t o_plan = al256(o_sig + sizeof(SigDesc) * (uint64_t)n_cands);
+    const uint64_t o_cdesc = al256(o_plan + sizeof(PieceRef) * (uint64_t)plan.size());
+    const uint64_t o_read = al256(o_cdesc + sizeof(CombineDesc) * (uint64_t)cdesc.size());
+    const uint64_t stage_need = al256(o_read + sizeof(int) * (uint64_t)n_cands) + 256;
+    if (h->stage_bytes < stage_need) {
+        if (h->stage)
+            cudaFreeHost(h->stage);
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        RA_CUDA(cudaHostAlloc((void **)&h->stage, stage_need, cudaHostAllocDefault));
+        h->stage_bytes = stage_need;
+    }
+    WorkDesc *work = (WorkDesc *)(h->stage + o_work);
+    SigDesc *sig_h = (SigDesc *)(h->stage + o_sig);
+    PieceRef *plan_h = (PieceRef *)(h->stage + o_plan);
+    CombineDesc *cdesc_h = (CombineDesc *)(h->stage + o_cdesc);
+    int *read_of = (int *)(h->stage + o_read);
+    parallel_for(b.n_work, [&](uint64_t x0, uint64_t x1) {
+        for (uint64_t x = x0; x < x1; ++x)
+            work[x] = items[order[x]].wd;
+    });
+    parallel_for(n_cands, [&](uint64_t c0, uint64_t c1) {
+        for (uint64_t c = c0; c < c1; ++c) {
+            sig_h[c] = sig[c];
+            read_of[c] = (int)cands[c].read_id;
+            if (b.anchored)
+                cdesc_h[c] = cdesc[c];
+        }
+    });
+    parallel_for(plan.size(), [&](uint64_t x0, uint64_t x1) {
+        if (x1 > x0)
+            memcpy(plan_h + x0, plan.data() + x0, sizeof(PieceRef) * (x1 - x0));
+    });
     // device memory
     b.d_events = take<float>(h, b, b.n_events);
     b.d_sig = take<SigDesc>(h, b, n_cands);
@@ -334,13 +375,13 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     // for them, and the host only for the copies themselves
     cudaStream_t s = h->upload;
     RA_CUDA(cudaMemcpyAsync(b.d_events, events, sizeof(float) * b.n_events, cudaMemcpyHostToDevice, s));
-    RA_CUDA(cudaMemcpyAsync(b.d_sig, sig.data(), sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
-    RA_CUDA(cudaMemcpyAsync(b.d_work, work.data(), sizeof(WorkDesc) * b.n_work, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(b.d_sig, sig_h, sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(b.d_work, work, sizeof(WorkDesc) * b.n_work, cudaMemcpyHostToDevice, s));
     if (b.anchored && !plan.empty())
-        RA_CUDA(cudaMemcpyAsync(b.d_plan, plan.data(), sizeof(PieceRef) * plan.size(), cudaMemcpyHostToDevice, s));
+        RA_CUDA(cudaMemcpyAsync(b.d_plan, plan_h, sizeof(PieceRef) * plan.size(), cudaMemcpyHostToDevice, s));
     if (b.anchored && n_cands)
-        RA_CUDA(cudaMemcpyAsync(b.d_cdesc, cdesc.data(), sizeof(CombineDesc) * n_cands, cudaMemcpyHostToDevice, s));
-    RA_CUDA(cudaMemcpyAsync(b.d_read_of, read_of.data(), sizeof(int) * n_cands, cudaMemcpyHostToDevice, s));
+        RA_CUDA(cudaMemcpyAsync(b.d_cdesc, cdesc_h, sizeof(CombineDesc) * n_cands, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(b.d_read_of, read_of, sizeof(int) * n_cands, cudaMemcpyHostToDevice, s));
     for (auto &e : b.ev)
         RA_CUDA(cudaEventCreate(&e));
     RA_CUDA(cudaEventRecord(h->uploaded, s));
@@ -818,6 +859,8 @@ extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
         cudaEventDestroy(h->fork);
     if (h->uploaded)
         cudaEventDestroy(h->uploaded);
+    if (h->stage)
+        cudaFreeHost(h->stage);
     if (h->upload)
         cudaStreamDestroy(h->upload);
     delete h;

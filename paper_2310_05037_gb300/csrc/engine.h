@@ -35,6 +35,23 @@ constexpr int kNumVariants = 10;
 constexpr int kMaxClasses = 64;              // launches per run (variant x ring size)
 constexpr size_t kSmemRingLimit = 96 * 1024; // larger rings go to global memory
 
+// Runs fn(lo, hi) over [0, n) on up to 16 host threads (one when n is small).
+template <typename F>
+inline void parallel_for(uint64_t n, F fn, uint64_t min_per_thread = 1 << 15)
+{
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const uint64_t T = std::max<uint64_t>(1, std::min<uint64_t>(std::min(hw, 16u), n / min_per_thread));
+    if (T == 1) {
+        fn((uint64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (uint64_t t = 0; t < T; ++t)
+        th.emplace_back(fn, n * t / T, n * (t + 1) / T);
+    for (auto &x : th)
+        x.join();
+}
+
 // ---------------------------------------------------------------- band math
 inline int64_t fdiv(int64_t a, int64_t b)
 {
@@ -242,6 +259,8 @@ struct rawalign_dtw {
     cudaStream_t aux[kMaxClasses] = {};   // one graph branch per launch class
     cudaStream_t upload = nullptr;         // batch uploads: overlap the previous batch's kernels
     cudaEvent_t uploaded = nullptr;
+    char *stage = nullptr;                 // pinned host staging for planned records (grown on demand)
+    size_t stage_bytes = 0;
     cudaEvent_t fork = nullptr, join[kMaxClasses] = {};
     int device = 0;
     int sm_count = 152;
