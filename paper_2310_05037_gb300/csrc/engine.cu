@@ -93,10 +93,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     b.anchored = anchor_offs != nullptr;
     if (b.anchored && !anchors && n_cands && anchor_offs[n_cands] != anchor_offs[0])
         return RA_EINVAL;
-    std::vector<PlanItem> items(b.anchored ? 0 : n_cands);
     std::vector<SigDesc> sig(n_cands);
-    std::vector<PieceRef> plan;
-    std::vector<CombineDesc> cdesc(b.anchored ? n_cands : 0);
     // pass 1 (sequential, cheap): candidate checks and each candidate's row
     // of expected values in the packed r array
     b.et = h->cfg.early_termination && !b.anchored && !b.plain && h->cfg.end_mode == RA_END_GLOBAL;
@@ -124,19 +121,133 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         sig[c].strand = cd.strand;
         r_total += (uint64_t)m;
     }
-    // pass 2 (threads over candidate ranges): band, work items and schedules;
-    // anchored chains are cut into pieces in thread-local lists, merged after
-    b.cells = 0;
-    b.max_rows = 1;
-    const int forced = h->cfg.kernel >= RA_KERNEL_VARIANT0 ? h->cfg.kernel - RA_KERNEL_VARIANT0 : -1;
+    // pass 2 runs on threads over candidate ranges; an anchored batch first
+    // counts each range's gaps and pieces, so that every range then writes
+    // its records straight to their final places
     struct Part {
         uint32_t c0 = 0, c1 = 0;
-        std::vector<PlanItem> items;
-        std::vector<PieceRef> plan;
+        uint64_t n_items = 0, n_plan = 0;  // this range's records
+        uint64_t ib = 0, pb = 0;           // their first global indices
         int max_rows = 1;
         int rc = RA_OK;
     };
-    auto plan_range = [&](Part &pt_) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const uint32_t n_parts = std::max<uint32_t>(1, std::min<uint32_t>(std::min(hw, 16u), (n_cands + 4095) / 4096));
+    std::vector<Part> parts(n_parts);
+    for (uint32_t t = 0; t < n_parts; ++t) {
+        parts[t].c0 = (uint32_t)((uint64_t)n_cands * t / n_parts);
+        parts[t].c1 = (uint32_t)((uint64_t)n_cands * (t + 1) / n_parts);
+    }
+    auto over_parts = [&](auto fn) {
+        parallel_for(n_parts, [&](uint64_t t0, uint64_t t1) {
+            for (uint64_t t = t0; t < t1; ++t)
+                fn(parts[t]);
+        }, 1);
+        for (auto &pt_ : parts)
+            if (pt_.rc != RA_OK)
+                return pt_.rc;
+        return (int)RA_OK;
+    };
+    // the pieces of one anchored candidate in path order (Sec. 2.4.2): gap 0,
+    // anchor 1, gap 1, ..., anchor K, gap K; each gap with rows and columns is
+    // a DTW work item, an anchor or a gap with only rows or only columns a
+    // fixed run of cells
+    auto gaps = [&](uint32_t c, auto on_gap, auto on_run) {
+        const rawalign_candidate_t &cd = cands[c];
+        const int64_t n = (int64_t)(offs[cd.read_id + 1] - offs[cd.read_id]);
+        const int64_t m = (int64_t)cd.ref_len_bases - k + 1;
+        const rawalign_anchor_t *A = anchors ? anchors + anchor_offs[c] : nullptr;
+        const uint64_t K = anchor_offs[c + 1] - anchor_offs[c];
+        int64_t pq = 0, pt = 0;
+        for (uint64_t a = 0; a <= K; ++a) {
+            const int64_t q1 = a < K ? (int64_t)A[a].q : n, t1 = a < K ? (int64_t)A[a].t : m;
+            const int64_t nr = q1 - pq, nc = t1 - pt;
+            if (nr > 0 && nc > 0) {
+                if (!on_gap(pq, pt, nr, nc))
+                    return false;
+            } else if (nr > 0) {
+                // events aligned to one value: the previous anchor's last (the first anchor's first)
+                on_run(pq, a > 0 ? pt - 1 : t1, nr, 1, 0);
+            } else if (nc > 0) {
+                // values aligned to one event: the previous anchor's last (the first anchor's first)
+                on_run(a > 0 ? pq - 1 : q1, pt, nc, 0, 1);
+            }
+            if (a < K) {
+                on_run((int64_t)A[a].q, (int64_t)A[a].t, (int64_t)A[a].len, 1, 1);
+                pq = (int64_t)A[a].q + A[a].len;
+                pt = (int64_t)A[a].t + A[a].len;
+            }
+        }
+        return true;
+    };
+    uint64_t n_items = n_cands, n_plan = 0;
+    if (b.anchored) {
+        int rc = over_parts([&](Part &pt_) {
+            for (uint32_t c = pt_.c0; c < pt_.c1; ++c) {
+                const rawalign_candidate_t &cd = cands[c];
+                const int64_t n = (int64_t)(offs[cd.read_id + 1] - offs[cd.read_id]);
+                const int64_t m = (int64_t)cd.ref_len_bases - k + 1;
+                const uint64_t K = anchor_offs[c + 1] - anchor_offs[c];
+                if (!anchors_valid(anchors ? anchors + anchor_offs[c] : nullptr, K, n, m)) {
+                    pt_.rc = RA_EINVAL;
+                    return;
+                }
+                gaps(
+                    c,
+                    [&](int64_t, int64_t, int64_t, int64_t) {
+                        ++pt_.n_items;
+                        ++pt_.n_plan;
+                        return true;
+                    },
+                    [&](int64_t, int64_t, int64_t, int, int) { ++pt_.n_plan; });
+            }
+        });
+        if (rc != RA_OK)
+            return rc;
+        n_items = 0;
+        for (auto &pt_ : parts) {
+            pt_.ib = n_items;
+            pt_.pb = n_plan;
+            n_items += pt_.n_items;
+            n_plan += pt_.n_plan;
+        }
+        if (n_plan >= (1ull << 32) || n_items >= (1ull << 31))
+            return RA_EINVAL;
+    } else {
+        for (auto &pt_ : parts)
+            pt_.ib = pt_.c0;
+    }
+    b.n_work = (uint32_t)n_items;
+    // planned records are written to a pinned staging buffer (one fast copy
+    // each); the plan items live in the handle's scratch, reused across batches
+    auto al256 = [](uint64_t x) { return (x + 255) & ~255ull; };
+    const uint64_t n_cdesc = b.anchored ? n_cands : 0;
+    const uint64_t o_work = 0, o_sig = al256(o_work + sizeof(WorkDesc) * n_items);
+    const uint64_t o_plan = al256(o_sig + sizeof(SigDesc) * (uint64_t)n_cands);
+    const uint64_t o_cdesc = al256(o_plan + sizeof(PieceRef) * n_plan);
+    const uint64_t o_read = al256(o_cdesc + sizeof(CombineDesc) * n_cdesc);
+    const uint64_t stage_need = al256(o_read + sizeof(int) * (uint64_t)n_cands) + 256;
+    if (h->stage_bytes < stage_need) {
+        if (h->stage)
+            cudaFreeHost(h->stage);
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        RA_CUDA(cudaHostAlloc((void **)&h->stage, stage_need, cudaHostAllocDefault));
+        h->stage_bytes = stage_need;
+    }
+    WorkDesc *work = (WorkDesc *)(h->stage + o_work);
+    SigDesc *sig_h = (SigDesc *)(h->stage + o_sig);
+    PieceRef *plan_h = (PieceRef *)(h->stage + o_plan);
+    CombineDesc *cdesc_h = (CombineDesc *)(h->stage + o_cdesc);
+    int *read_of = (int *)(h->stage + o_read);
+    if (h->plan_items.size() < n_items)
+        h->plan_items.resize(n_items);
+    PlanItem *items = h->plan_items.data();
+    // band, work items and schedules
+    b.cells = 0;
+    b.max_rows = 1;
+    const int forced = h->cfg.kernel >= RA_KERNEL_VARIANT0 ? h->cfg.kernel - RA_KERNEL_VARIANT0 : -1;
+    int rc = over_parts([&](Part &pt_) {
         auto schedule_item = [&](PlanItem &it, const BandDef &band, int64_t n) {
             Sched sc;
             if (b.plain || (forced >= 0 && forced < kNumVariants)) {
@@ -145,9 +256,11 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
             } else {
                 it.variant = choose_variant(band, 0, n, sc, h->slot_cost);
             }
+            it.wave = 0;
             set_schedule(it, sc);
             pt_.max_rows = std::max<int>(pt_.max_rows, (int)n);
         };
+        uint64_t ix = pt_.ib, px = pt_.pb;
         for (uint32_t c = pt_.c0; c < pt_.c1; ++c) {
             const rawalign_candidate_t &cd = cands[c];
             const int64_t n = (int64_t)(offs[cd.read_id + 1] - offs[cd.read_id]);
@@ -167,164 +280,66 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
                 it.wave = (b.et && first_of_read[cd.read_id] != c) ? 1 : 0;
                 continue;
             }
-            // Sec. 2.4.2: gap 0, anchor 1, gap 1, ..., anchor K, gap K in path order
-            const rawalign_anchor_t *A = anchors ? anchors + anchor_offs[c] : nullptr;
-            const uint64_t K = anchor_offs[c + 1] - anchor_offs[c];
-            if (!anchors_valid(A, K, n, m)) {
-                pt_.rc = RA_EINVAL;
-                return;
-            }
-            CombineDesc &cdc = cdesc[c];
-            cdc.first = (uint32_t)pt_.plan.size();  // part-local until the merge
+            CombineDesc &cdc = cdesc_h[c];
+            cdc.first = (uint32_t)px;
             cdc.n = (int32_t)n;
             cdc.m = (int32_t)m;
             cdc.read = (int32_t)cd.read_id;
             cdc.w_report = cd.band_w < 0 ? -1 : cd.band_w;
-            int64_t pq = 0, pt = 0;
-            for (uint64_t a = 0; a <= K; ++a) {
-                const int64_t q1 = a < K ? (int64_t)A[a].q : n, t1 = a < K ? (int64_t)A[a].t : m;
-                const int64_t nr = q1 - pq, nc = t1 - pt;
-                PieceRef pr{};
-                if (nr > 0 && nc > 0) {
+            const bool ok = gaps(
+                c,
+                [&](int64_t pq, int64_t pt, int64_t nr, int64_t nc) {
+                    // a gap aligned by banded DTW into its own result slot
                     BandDef gb;
                     int32_t gw;
-                    if (band_for(nr, nc, cd.band_w, 0, 0, gb, gw) != 0) {
-                        pt_.rc = RA_EINVAL;
-                        return;
-                    }
-                    PlanItem it;
-                    const int32_t slot = (int32_t)pt_.items.size();  // part-local until the merge
+                    if (band_for(nr, nc, cd.band_w, 0, 0, gb, gw) != 0)
+                        return false;
+                    const int32_t slot = (int32_t)ix++;
+                    PlanItem &it = items[slot];
                     fill_work(it, ev0 + pq, r0 + pt, nr, nc, gb, gw, slot, slot, (int32_t)nr);
                     schedule_item(it, gb, nr);
-                    pt_.items.push_back(it);
+                    PieceRef pr{};
                     pr.kind = 0;
                     pr.idx = (uint32_t)slot;
-                    pt_.plan.push_back(pr);
-                } else if (nr > 0) {
-                    // events aligned to one value: the previous anchor's last (the first anchor's first)
+                    plan_h[px++] = pr;
+                    return true;
+                },
+                [&](int64_t q, int64_t t, int64_t len, int ev_step, int r_step) {
+                    PieceRef pr{};
                     pr.kind = 1;
-                    pr.ev = ev0 + pq;
-                    pr.r = r0 + (a > 0 ? pt - 1 : t1);
-                    pr.len = (uint32_t)nr;
-                    pr.ev_step = 1;
-                    pr.r_step = 0;
-                    pt_.plan.push_back(pr);
-                } else if (nc > 0) {
-                    // values aligned to one event: the previous anchor's last (the first anchor's first)
-                    pr.kind = 1;
-                    pr.ev = ev0 + (a > 0 ? pq - 1 : q1);
-                    pr.r = r0 + pt;
-                    pr.len = (uint32_t)nc;
-                    pr.ev_step = 0;
-                    pr.r_step = 1;
-                    pt_.plan.push_back(pr);
-                }
-                if (a < K) {
-                    pr = PieceRef{};
-                    pr.kind = 1;
-                    pr.ev = ev0 + A[a].q;
-                    pr.r = r0 + A[a].t;
-                    pr.len = A[a].len;
-                    pr.ev_step = 1;
-                    pr.r_step = 1;
-                    pt_.plan.push_back(pr);
-                    pq = (int64_t)A[a].q + A[a].len;
-                    pt = (int64_t)A[a].t + A[a].len;
-                }
+                    pr.ev = ev0 + q;
+                    pr.r = r0 + t;
+                    pr.len = (uint32_t)len;
+                    pr.ev_step = (uint16_t)ev_step;
+                    pr.r_step = (uint16_t)r_step;
+                    plan_h[px++] = pr;
+                });
+            if (!ok) {
+                pt_.rc = RA_EINVAL;
+                return;
             }
-            cdc.count = (uint32_t)pt_.plan.size() - cdc.first;
+            cdc.count = (uint32_t)(px - cdc.first);
         }
-    };
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const uint32_t n_parts = std::max<uint32_t>(1, std::min<uint32_t>(std::min(hw, 16u), (n_cands + 4095) / 4096));
-    std::vector<Part> parts(n_parts);
-    for (uint32_t t = 0; t < n_parts; ++t) {
-        parts[t].c0 = (uint32_t)((uint64_t)n_cands * t / n_parts);
-        parts[t].c1 = (uint32_t)((uint64_t)n_cands * (t + 1) / n_parts);
-    }
-    if (n_parts == 1) {
-        plan_range(parts[0]);
-    } else {
-        std::vector<std::thread> th;
-        for (uint32_t t = 0; t < n_parts; ++t)
-            th.emplace_back(plan_range, std::ref(parts[t]));
-        for (auto &x : th)
-            x.join();
-    }
-    uint64_t n_items = 0, n_plan = 0;
-    for (auto &pt_ : parts) {
-        if (pt_.rc != RA_OK)
-            return pt_.rc;
+    });
+    if (rc != RA_OK)
+        return rc;
+    for (auto &pt_ : parts)
         b.max_rows = std::max(b.max_rows, pt_.max_rows);
-        n_items += pt_.items.size();
-        n_plan += pt_.plan.size();
-    }
-    if (b.anchored) {
-        if (n_plan >= (1ull << 32) || n_items >= (1ull << 31))
-            return RA_EINVAL;
-        items.resize(n_items);
-        plan.resize(n_plan);
-        std::vector<uint64_t> ibase(parts.size() + 1, 0), pbase(parts.size() + 1, 0);
-        for (size_t t = 0; t < parts.size(); ++t) {
-            ibase[t + 1] = ibase[t] + parts[t].items.size();
-            pbase[t + 1] = pbase[t] + parts[t].plan.size();
-        }
-        // each part moves its items and pieces into place in parallel
-        parallel_for(parts.size(), [&](uint64_t t0, uint64_t t1) {
-            for (uint64_t t = t0; t < t1; ++t) {
-                Part &pt_ = parts[t];
-                const uint32_t ib = (uint32_t)ibase[t], pb = (uint32_t)pbase[t];
-                for (size_t x = 0; x < pt_.items.size(); ++x) {
-                    PlanItem &it = items[ib + x];
-                    it = pt_.items[x];
-                    it.wd.cand += (int32_t)ib;
-                    it.wd.read += (int32_t)ib;
-                }
-                for (size_t x = 0; x < pt_.plan.size(); ++x) {
-                    PieceRef pr = pt_.plan[x];
-                    if (pr.kind == 0)
-                        pr.idx += ib;
-                    plan[pb + x] = pr;
-                }
-                for (uint32_t c = pt_.c0; c < pt_.c1; ++c)
-                    cdesc[c].first += pb;
-            }
-        }, 1);
-    }
-    b.n_work = (uint32_t)items.size();
     if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO)
-        shorten_longest(items, h->sm_count, h->slot_cost);
+        shorten_longest(items, n_items, h->sm_count, h->slot_cost);
+    uint64_t slots[kNumVariants];
+    variant_slots(items, n_items, slots);
     b.slots = 0;
-    for (const PlanItem &it : items)
-        b.slots += (uint64_t)std::max(it.wd.s_end, 0) * kVariants[it.variant][0] * kVariants[it.variant][1];
+    for (int v = 0; v < kNumVariants; ++v)
+        b.slots += slots[v];
     // launch order and classes (variant x ring size), longest first
-    std::vector<int> order;
+    std::vector<int> &order = h->plan_order;
     b.classes.clear();
-    if (!make_classes(items, order, b.classes))
+    if (!make_classes(items, n_items, order, b.classes))
         return RA_EINVAL;
     if (b.plain)
         b.classes.clear();
-    // planned records go through a pinned staging buffer: one fast copy each
-    auto al256 = [](uint64_t x) { return (x + 255) & ~255ull; };
-    const uint64_t o_work = 0, o_sig = al256(o_work + sizeof(WorkDesc) * (uint64_t)b.n_work);
-    const uint64_t o_plan = al256(o_sig + sizeof(SigDesc) * (uint64_t)n_cands);
-    const uint64_t o_cdesc = al256(o_plan + sizeof(PieceRef) * (uint64_t)plan.size());
-    const uint64_t o_read = al256(o_cdesc + sizeof(CombineDesc) * (uint64_t)cdesc.size());
-    const uint64_t stage_need = al256(o_read + sizeof(int) * (uint64_t)n_cands) + 256;
-    if (h->stage_bytes < stage_need) {
-        if (h->stage)
-            cudaFreeHost(h->stage);
-        h->stage = nullptr;
-        h->stage_bytes = 0;
-        RA_CUDA(cudaHostAlloc((void **)&h->stage, stage_need, cudaHostAllocDefault));
-        h->stage_bytes = stage_need;
-    }
-    WorkDesc *work = (WorkDesc *)(h->stage + o_work);
-    SigDesc *sig_h = (SigDesc *)(h->stage + o_sig);
-    PieceRef *plan_h = (PieceRef *)(h->stage + o_plan);
-    CombineDesc *cdesc_h = (CombineDesc *)(h->stage + o_cdesc);
-    int *read_of = (int *)(h->stage + o_read);
-    parallel_for(b.n_work, [&](uint64_t x0, uint64_t x1) {
+    parallel_for(n_items, [&](uint64_t x0, uint64_t x1) {
         for (uint64_t x = x0; x < x1; ++x)
             work[x] = items[order[x]].wd;
     });
@@ -332,13 +347,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         for (uint64_t c = c0; c < c1; ++c) {
             sig_h[c] = sig[c];
             read_of[c] = (int)cands[c].read_id;
-            if (b.anchored)
-                cdesc_h[c] = cdesc[c];
         }
-    });
-    parallel_for(plan.size(), [&](uint64_t x0, uint64_t x1) {
-        if (x1 > x0)
-            memcpy(plan_h + x0, plan.data() + x0, sizeof(PieceRef) * (x1 - x0));
     });
     // device memory
     b.d_events = take<float>(h, b, b.n_events);
@@ -356,7 +365,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     if (b.anchored) {
         b.d_pres = take<rawalign_result_t>(h, b, b.n_work);
         b.d_pkeys = take<unsigned long long>(h, b, b.n_work);
-        b.d_plan = take<PieceRef>(h, b, plan.size());
+        b.d_plan = take<PieceRef>(h, b, n_plan);
         b.d_cdesc = take<CombineDesc>(h, b, n_cands);
         if (!b.d_pres || !b.d_pkeys || !b.d_plan || !b.d_cdesc)
             return RA_ENOMEM;
@@ -367,7 +376,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
             return RA_ENOMEM;
     }
     // launch geometry and global rings where shared memory is too small
-    int rc = finalize_classes(h->sm_count, b.classes, [&](uint64_t bytes) { return (void *)take<char>(h, b, bytes); });
+    rc = finalize_classes(h->sm_count, b.classes, [&](uint64_t bytes) { return (void *)take<char>(h, b, bytes); });
     if (rc != RA_OK)
         return rc;
     // uploads go on their own stream so that planning and copying this batch
@@ -377,8 +386,8 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     RA_CUDA(cudaMemcpyAsync(b.d_events, events, sizeof(float) * b.n_events, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_sig, sig_h, sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_work, work, sizeof(WorkDesc) * b.n_work, cudaMemcpyHostToDevice, s));
-    if (b.anchored && !plan.empty())
-        RA_CUDA(cudaMemcpyAsync(b.d_plan, plan_h, sizeof(PieceRef) * plan.size(), cudaMemcpyHostToDevice, s));
+    if (b.anchored && n_plan)
+        RA_CUDA(cudaMemcpyAsync(b.d_plan, plan_h, sizeof(PieceRef) * n_plan, cudaMemcpyHostToDevice, s));
     if (b.anchored && n_cands)
         RA_CUDA(cudaMemcpyAsync(b.d_cdesc, cdesc_h, sizeof(CombineDesc) * n_cands, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_read_of, read_of, sizeof(int) * n_cands, cudaMemcpyHostToDevice, s));

@@ -194,7 +194,7 @@ struct Arena {
 
 struct ClassLaunch {
     int G = 0, HR = 0;
-    double max_cost = 0;       // lane-steps of the class's largest alignment
+    double max_cost = 0;       // lane-steps of the class's largest alignment (steps x lanes, empty as 0)
     int first = 0, count = 0;  // range in the sorted work array
     int ring_cap = 0;
     int ring_in_smem = 1;
@@ -247,6 +247,15 @@ struct Ticket {
     bool serving = false;
 };
 
+// One piece of work as planned on the host.
+struct PlanItem {
+    WorkDesc wd;
+    int wave = 0;       // early termination: 0 = first candidate of its read (queued first), 1 = the others
+    int variant = 0;
+    int cap = 0;        // ring entries the piece needs (power of two)
+    double cost = 0;    // lane-steps: longest first
+};
+
 struct ServeState;
 
 }  // namespace ra_host
@@ -261,6 +270,8 @@ struct rawalign_dtw {
     cudaEvent_t uploaded = nullptr;
     char *stage = nullptr;                 // pinned host staging for planned records (grown on demand)
     size_t stage_bytes = 0;
+    std::vector<ra_host::PlanItem> plan_items;  // planning scratch, reused across batches
+    std::vector<int> plan_order;
     cudaEvent_t fork = nullptr, join[kMaxClasses] = {};
     int device = 0;
     int sm_count = 152;
@@ -325,15 +336,6 @@ inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &o
     return best;
 }
 
-// One piece of work as planned on the host.
-struct PlanItem {
-    WorkDesc wd;
-    int wave = 0;       // early termination: 0 = first candidate of its read (queued first), 1 = the others
-    int variant = 0;
-    int cap = 0;        // ring entries the piece needs (power of two)
-    double cost = 0;    // lane-steps: longest first
-};
-
 inline int ring_need(const WorkDesc &wd, int G);
 
 inline void set_schedule(PlanItem &it, const Sched &s)
@@ -357,44 +359,66 @@ inline void set_schedule(PlanItem &it, const Sched &s)
 // of 32 lanes finishes them in about half the time.  (Measured on a GB300:
 // the half-estimate rule gives +15 % on 4,000 long reads and -10 % on 90,000
 // uneven alignments, hence the switch.)
-inline void shorten_longest(std::vector<PlanItem> &items, int sm_count, const double *cost)
+// Lane-cell slots (steps x lanes x rows, empty items as 0) per variant:
+// integers, so the sums do not depend on how the items are split over threads.
+inline void variant_slots(const PlanItem *items, size_t n, uint64_t out[kNumVariants])
 {
+    std::mutex mu;
+    for (int v = 0; v < kNumVariants; ++v)
+        out[v] = 0;
+    parallel_for(n, [&](uint64_t lo, uint64_t hi) {
+        uint64_t acc[kNumVariants] = {};
+        for (uint64_t x = lo; x < hi; ++x)
+            acc[items[x].variant] += (uint64_t)std::max(items[x].wd.s_end, 0) * kVariants[items[x].variant][0] *
+                                     kVariants[items[x].variant][1];
+        std::lock_guard<std::mutex> g(mu);
+        for (int v = 0; v < kNumVariants; ++v)
+            out[v] += acc[v];
+    });
+}
+
+inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const double *cost)
+{
+    uint64_t slots[kNumVariants];
+    variant_slots(items, n, slots);
     double total = 0;
-    for (const PlanItem &it : items)
-        total += (double)std::max(it.wd.s_end, 0) * kVariants[it.variant][0] * kVariants[it.variant][1] *
-                 cost[it.variant];
+    for (int v = 0; v < kNumVariants; ++v)
+        total += (double)slots[v] * cost[v];
     const double groups = 32.0 * std::max(sm_count, 1);
-    const double theta = (double)items.size() < 4.0 * groups ? 0.5 : 1.0;
+    const double theta = (double)n < 4.0 * groups ? 0.5 : 1.0;
     const double batch_len = theta * total / (512.0 * std::max(sm_count, 1));
-    for (PlanItem &it : items) {
-        const int v0 = it.variant;
-        const double dur = (double)it.wd.s_end * kVariants[v0][1] * cost[v0];
-        if (it.wd.s_end <= 0 || kVariants[v0][0] == 32 || dur <= batch_len)
-            continue;
-        BandDef band;
-        band.num = it.wd.num;
-        band.den = it.wd.den;
-        band.w = it.wd.w;
-        band.m = it.wd.m;
-        int best = -1;
-        double best_score = -1;
-        Sched best_s;
-        for (int v = 0; v < kNumVariants; ++v) {
-            if (kVariants[v][0] != 32)
+    parallel_for(n, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t x = lo; x < hi; ++x) {
+            PlanItem &it = items[x];
+            const int v0 = it.variant;
+            const double dur = (double)it.wd.s_end * kVariants[v0][1] * cost[v0];
+            if (it.wd.s_end <= 0 || kVariants[v0][0] == 32 || dur <= batch_len)
                 continue;
-            Sched s = schedule(band, it.wd.row0, it.wd.nrows, 32, kVariants[v][1]);
-            const double score = s.eff / cost[v];
-            if (s.s_end > 0 && score > best_score) {
-                best_score = score;
-                best = v;
-                best_s = s;
+            BandDef band;
+            band.num = it.wd.num;
+            band.den = it.wd.den;
+            band.w = it.wd.w;
+            band.m = it.wd.m;
+            int best = -1;
+            double best_score = -1;
+            Sched best_s;
+            for (int v = 0; v < kNumVariants; ++v) {
+                if (kVariants[v][0] != 32)
+                    continue;
+                Sched s = schedule(band, it.wd.row0, it.wd.nrows, 32, kVariants[v][1]);
+                const double score = s.eff / cost[v];
+                if (s.s_end > 0 && score > best_score) {
+                    best_score = score;
+                    best = v;
+                    best_s = s;
+                }
             }
+            if (best < 0 || (double)best_s.s_end * kVariants[best][1] * cost[best] >= dur)
+                continue;
+            it.variant = best;
+            set_schedule(it, best_s);
         }
-        if (best < 0 || (double)best_s.s_end * kVariants[best][1] * cost[best] >= dur)
-            continue;
-        it.variant = best;
-        set_schedule(it, best_s);
-    }
+    });
 }
 
 // Sorts the items into launch order (variant, ring size, longest first) and
@@ -403,58 +427,57 @@ inline void shorten_longest(std::vector<PlanItem> &items, int sm_count, const do
 // resident blocks, or a ring in global memory) on everything else.  Classes
 // are returned longest-alignment first.  Returns false if more than
 // kMaxClasses would be needed.
-inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &order, std::vector<ClassLaunch> &classes)
+inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &order, std::vector<ClassLaunch> &classes)
 {
-    // Launch order: counting sort by (variant, ring size, wave), then within
-    // each bucket a stable radix sort by steps, longest first.  Exact order
-    // by length matters: the groups of a warp run in lockstep until the first
-    // of them finishes, so neighbours in the queue should finish together.
-    // With early termination each bucket holds the reads' first candidates
-    // before the others.  Linear in the number of items and deterministic.
-    const size_t n = items.size();
-    constexpr int kCaps = 8;
+    // Launch order: a stable LSD radix sort (16-bit digits) on one 64-bit key
+    // per item, the bucket (variant, ring size, wave) above the complemented
+    // step count, so ascending keys are longest first within a bucket and
+    // equal keys keep item order.  Exact order by length matters: the groups
+    // of a warp run in lockstep until the first of them finishes, so
+    // neighbours in the queue should finish together.  With early termination
+    // each bucket holds the reads' first candidates before the others.
+    // Linear in the number of items and deterministic.
+    constexpr int kCaps = 12;  // ring sizes 128 << 2i
     auto cap_index = [](int cap) {
         int i = 0;
-        while (i < kCaps - 1 && (128 << (2 * i)) < cap)
+        while (i < kCaps - 1 && (128ll << (2 * i)) < cap)
             ++i;
         return i;
     };
-    const int n_keys = kNumVariants * kCaps * 2;
-    std::vector<uint32_t> start(n_keys + 1, 0);
-    std::vector<int> keys(n);
-    for (size_t x = 0; x < n; ++x) {
-        keys[x] = (items[x].variant * kCaps + cap_index(items[x].cap)) * 2 + items[x].wave;
-        ++start[keys[x] + 1];
-    }
-    for (int q = 0; q < n_keys; ++q)
-        start[q + 1] += start[q];
-    std::vector<uint32_t> bucket_lo(start.begin(), start.end());
+    std::vector<uint64_t> key(n), key2(n);
+    std::vector<int> tmp(n);
     order.resize(n);
-    for (size_t x = 0; x < n; ++x)
-        order[start[keys[x]]++] = (int)x;
-    std::vector<int> tmp;
-    std::vector<uint32_t> cnt(1 << 16);
-    for (int q = 0; q < n_keys; ++q) {
-        const uint32_t lo = bucket_lo[q], hi = bucket_lo[q + 1];
-        if (hi - lo < 2)
-            continue;
-        tmp.resize(hi - lo);
-        auto rkey = [&](int x) { return ~(uint32_t)std::max(items[x].wd.s_end, 0); };  // ascending = longest first
-        for (int shift = 0; shift < 32; shift += 16) {
-            std::fill(cnt.begin(), cnt.end(), 0u);
-            for (uint32_t y = lo; y < hi; ++y)
-                ++cnt[(rkey(order[y]) >> shift) & 0xFFFF];
-            uint32_t acc = 0;
-            for (auto &c : cnt) {
-                const uint32_t t = c;
-                c = acc;
-                acc += t;
-            }
-            for (uint32_t y = lo; y < hi; ++y)
-                tmp[cnt[(rkey(order[y]) >> shift) & 0xFFFF]++] = order[y];
-            std::copy(tmp.begin(), tmp.end(), order.begin() + lo);
+    parallel_for(n, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t x = lo; x < hi; ++x) {
+            const PlanItem &it = items[x];
+            const uint64_t bucket = (uint64_t)((it.variant * kCaps + cap_index(it.cap)) * 2 + it.wave);
+            key[x] = bucket << 32 | (uint64_t)~(uint32_t)std::max(it.wd.s_end, 0);
+            order[x] = (int)x;
         }
+    });
+    std::vector<uint32_t> cnt(1 << 16);
+    for (int shift = 0; shift < 48 && n > 1; shift += 16) {
+        std::fill(cnt.begin(), cnt.end(), 0u);
+        for (size_t x = 0; x < n; ++x)
+            ++cnt[(key[x] >> shift) & 0xFFFF];
+        if (cnt[(key[0] >> shift) & 0xFFFF] == n)
+            continue;  // one value of this digit: the pass would move nothing
+        uint32_t acc = 0;
+        for (auto &c : cnt) {
+            const uint32_t t = c;
+            c = acc;
+            acc += t;
+        }
+        for (size_t x = 0; x < n; ++x) {
+            const uint32_t y = cnt[(key[x] >> shift) & 0xFFFF]++;
+            key2[y] = key[x];
+            tmp[y] = order[x];
+        }
+        key.swap(key2);
+        order.swap(tmp);
     }
+    // classes: runs of one (variant, ring size); a class's longest item heads
+    // one of its two wave runs
     classes.clear();
     size_t pos = 0;
     while (pos < n) {
@@ -464,11 +487,11 @@ inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &o
         cl.HR = kVariants[f.variant][1];
         cl.first = (int)pos;
         cl.ring_cap = f.cap;
-        cl.max_cost = f.cost;
-        while (pos < n && items[order[pos]].variant == f.variant && items[order[pos]].cap == f.cap) {
-            cl.max_cost = std::max(cl.max_cost, items[order[pos]].cost);
-            ++pos;
-        }
+        cl.max_cost = 0;
+        const uint64_t id = key[pos] >> 33;
+        for (; pos < n && (key[pos] >> 33) == id; ++pos)
+            if ((int)pos == cl.first || (key[pos] >> 32) != (key[pos - 1] >> 32))
+                cl.max_cost = std::max(cl.max_cost, (double)(uint32_t)~(uint32_t)key[pos] * cl.G);
         cl.count = (int)pos - cl.first;
         classes.push_back(cl);
     }
@@ -477,6 +500,11 @@ inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &o
     std::stable_sort(classes.begin(), classes.end(),
                      [](const ClassLaunch &x, const ClassLaunch &y) { return x.max_cost > y.max_cost; });
     return true;
+}
+
+inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &order, std::vector<ClassLaunch> &classes)
+{
+    return make_classes(items.data(), items.size(), order, classes);
 }
 
 // Ring entries one piece needs: the stripe period plus two (written one step
