@@ -455,24 +455,49 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
             order[x] = (int)x;
         }
     });
-    std::vector<uint32_t> cnt(1 << 16);
+    // each pass: per-chunk digit counts, offsets in (digit, chunk) order,
+    // then every chunk scatters its items in order (stable)
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t T = std::max<size_t>(1, std::min<size_t>(std::min(hw, 16u), n / (1 << 16)));
+    std::vector<uint32_t> cnt(T << 16);
+    auto chunks = [&](auto fn) {
+        if (T == 1) {
+            fn((size_t)0);
+            return;
+        }
+        std::vector<std::thread> th;
+        for (size_t t = 0; t < T; ++t)
+            th.emplace_back(fn, t);
+        for (auto &x : th)
+            x.join();
+    };
     for (int shift = 0; shift < 48 && n > 1; shift += 16) {
-        std::fill(cnt.begin(), cnt.end(), 0u);
-        for (size_t x = 0; x < n; ++x)
-            ++cnt[(key[x] >> shift) & 0xFFFF];
-        if (cnt[(key[0] >> shift) & 0xFFFF] == n)
+        chunks([&](size_t t) {
+            uint32_t *c = cnt.data() + (t << 16);
+            std::fill(c, c + (1 << 16), 0u);
+            for (size_t x = n * t / T; x < n * (t + 1) / T; ++x)
+                ++c[(key[x] >> shift) & 0xFFFF];
+        });
+        uint64_t first_digit = 0;
+        for (size_t t = 0; t < T; ++t)
+            first_digit += cnt[(t << 16) + ((key[0] >> shift) & 0xFFFF)];
+        if (first_digit == n)
             continue;  // one value of this digit: the pass would move nothing
         uint32_t acc = 0;
-        for (auto &c : cnt) {
-            const uint32_t t = c;
-            c = acc;
-            acc += t;
-        }
-        for (size_t x = 0; x < n; ++x) {
-            const uint32_t y = cnt[(key[x] >> shift) & 0xFFFF]++;
-            key2[y] = key[x];
-            tmp[y] = order[x];
-        }
+        for (size_t d = 0; d < (1 << 16); ++d)
+            for (size_t t = 0; t < T; ++t) {
+                const uint32_t c = cnt[(t << 16) + d];
+                cnt[(t << 16) + d] = acc;
+                acc += c;
+            }
+        chunks([&](size_t t) {
+            uint32_t *c = cnt.data() + (t << 16);
+            for (size_t x = n * t / T; x < n * (t + 1) / T; ++x) {
+                const uint32_t y = c[(key[x] >> shift) & 0xFFFF]++;
+                key2[y] = key[x];
+                tmp[y] = order[x];
+            }
+        });
         key.swap(key2);
         order.swap(tmp);
     }
