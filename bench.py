@@ -238,6 +238,12 @@ def main():
     arena = 3 * need + len(w.ref2bit) + (256 << 20)  # the prepared batch and two submissions in flight
     if w.anchor_offsets is not None:  # per-gap work items and results, pieces
         arena += 3 * (len(w.anchors) + w.n_cands) * 512
+    m_c = w.cands["ref_len_bases"].astype(np.int64) - w.k + 1
+    w_c = np.where(w.cands["band_w"] < 0, m_c, w.cands["band_w"].astype(np.int64))
+    if w.n_cands and int(np.max(2 * w_c + 1)) > 2000:
+        # bands too wide for shared-memory rings take ring scratch from the
+        # arena beyond batch_bytes; room for full grids in each batch
+        arena += 3 * (2 << 30)
     al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena, device="cuda:%d" % local,
                    early_termination=args.workload == "batched_et")
     stream = al.stream

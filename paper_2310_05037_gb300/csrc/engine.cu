@@ -93,41 +93,19 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     b.anchored = anchor_offs != nullptr;
     if (b.anchored && !anchors && n_cands && anchor_offs[n_cands] != anchor_offs[0])
         return RA_EINVAL;
-    std::vector<SigDesc> sig(n_cands);
-    // pass 1 (sequential, cheap): candidate checks and each candidate's row
-    // of expected values in the packed r array
+    // anchor offsets must not decrease: checked before any range reads anchors
+    if (b.anchored)
+        for (uint32_t c = 0; c < n_cands; ++c)
+            if (anchor_offs[c + 1] < anchor_offs[c])
+                return RA_EINVAL;
     b.et = h->cfg.early_termination && !b.anchored && !b.plain && h->cfg.end_mode == RA_END_GLOBAL;
-    std::vector<uint32_t> first_of_read(b.et ? n_reads : 0, UINT32_MAX);
-    uint64_t r_total = 0;
-    for (uint32_t c = 0; c < n_cands; ++c) {
-        const rawalign_candidate_t &cd = cands[c];
-        if (cd.read_id >= n_reads || cd.strand > 1)
-            return RA_EINVAL;
-        if (cd.ref_offset > h->ref_len || cd.ref_len_bases > h->ref_len - cd.ref_offset)
-            return RA_EINVAL;
-        if ((int64_t)cd.ref_len_bases < k)
-            return RA_EINVAL;
-        const int64_t n = (int64_t)(offs[cd.read_id + 1] - offs[cd.read_id]);
-        const int64_t m = (int64_t)cd.ref_len_bases - k + 1;
-        if (n >= (1 << 30) || m >= (1 << 30))
-            return RA_EINVAL;
-        if (b.anchored && anchor_offs[c + 1] < anchor_offs[c])
-            return RA_EINVAL;
-        if (b.et && first_of_read[cd.read_id] == UINT32_MAX)
-            first_of_read[cd.read_id] = c;
-        sig[c].ref_off = cd.ref_offset;
-        sig[c].r_off = r_total;
-        sig[c].len = cd.ref_len_bases;
-        sig[c].strand = cd.strand;
-        r_total += (uint64_t)m;
-    }
-    // pass 2 runs on threads over candidate ranges; an anchored batch first
-    // counts each range's gaps and pieces, so that every range then writes
-    // its records straight to their final places
+    // planning runs on threads over candidate ranges: checks and sizes first,
+    // then every range writes its records straight to their final places
     struct Part {
         uint32_t c0 = 0, c1 = 0;
+        uint64_t r_sum = 0;                // expected values of the range
         uint64_t n_items = 0, n_plan = 0;  // this range's records
-        uint64_t ib = 0, pb = 0;           // their first global indices
+        uint64_t rb = 0, ib = 0, pb = 0;   // their first global indices
         int max_rows = 1;
         int rc = RA_OK;
     };
@@ -180,53 +158,70 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         }
         return true;
     };
-    uint64_t n_items = n_cands, n_plan = 0;
-    if (b.anchored) {
-        int rc = over_parts([&](Part &pt_) {
-            for (uint32_t c = pt_.c0; c < pt_.c1; ++c) {
-                const rawalign_candidate_t &cd = cands[c];
-                const int64_t n = (int64_t)(offs[cd.read_id + 1] - offs[cd.read_id]);
-                const int64_t m = (int64_t)cd.ref_len_bases - k + 1;
-                const uint64_t K = anchor_offs[c + 1] - anchor_offs[c];
-                if (!anchors_valid(anchors ? anchors + anchor_offs[c] : nullptr, K, n, m)) {
-                    pt_.rc = RA_EINVAL;
-                    return;
-                }
-                gaps(
-                    c,
-                    [&](int64_t, int64_t, int64_t, int64_t) {
-                        ++pt_.n_items;
-                        ++pt_.n_plan;
-                        return true;
-                    },
-                    [&](int64_t, int64_t, int64_t, int, int) { ++pt_.n_plan; });
+    // pass 1: candidate checks, expected values per range, and (anchored)
+    // the exact count of gaps and pieces
+    int rc = over_parts([&](Part &pt_) {
+        for (uint32_t c = pt_.c0; c < pt_.c1; ++c) {
+            const rawalign_candidate_t &cd = cands[c];
+            if (cd.read_id >= n_reads || cd.strand > 1 || cd.ref_offset > h->ref_len ||
+                cd.ref_len_bases > h->ref_len - cd.ref_offset || (int64_t)cd.ref_len_bases < k) {
+                pt_.rc = RA_EINVAL;
+                return;
             }
-        });
-        if (rc != RA_OK)
-            return rc;
-        n_items = 0;
-        for (auto &pt_ : parts) {
-            pt_.ib = n_items;
-            pt_.pb = n_plan;
-            n_items += pt_.n_items;
-            n_plan += pt_.n_plan;
+            const int64_t n = (int64_t)(offs[cd.read_id + 1] - offs[cd.read_id]);
+            const int64_t m = (int64_t)cd.ref_len_bases - k + 1;
+            if (n >= (1 << 30) || m >= (1 << 30)) {
+                pt_.rc = RA_EINVAL;
+                return;
+            }
+            pt_.r_sum += (uint64_t)m;
+            if (!b.anchored)
+                continue;
+            const uint64_t K = anchor_offs[c + 1] - anchor_offs[c];
+            if (!anchors_valid(anchors ? anchors + anchor_offs[c] : nullptr, K, n, m)) {
+                pt_.rc = RA_EINVAL;
+                return;
+            }
+            gaps(
+                c,
+                [&](int64_t, int64_t, int64_t, int64_t) {
+                    ++pt_.n_items;
+                    ++pt_.n_plan;
+                    return true;
+                },
+                [&](int64_t, int64_t, int64_t, int, int) { ++pt_.n_plan; });
         }
-        if (n_plan >= (1ull << 32) || n_items >= (1ull << 31))
-            return RA_EINVAL;
-    } else {
-        for (auto &pt_ : parts)
-            pt_.ib = pt_.c0;
+        if (!b.anchored)
+            pt_.n_items = pt_.c1 - pt_.c0;
+    });
+    if (rc != RA_OK)
+        return rc;
+    uint64_t r_total = 0, n_items = 0, n_plan = 0;
+    for (auto &pt_ : parts) {
+        pt_.rb = r_total;
+        pt_.ib = n_items;
+        pt_.pb = n_plan;
+        r_total += pt_.r_sum;
+        n_items += pt_.n_items;
+        n_plan += pt_.n_plan;
     }
+    if (n_plan >= (1ull << 32) || n_items >= (1ull << 31))
+        return RA_EINVAL;
+    // early termination queues each read's first candidate first
+    std::vector<uint32_t> first_of_read(b.et ? n_reads : 0, UINT32_MAX);
+    if (b.et)
+        for (uint32_t c = n_cands; c-- > 0;)
+            first_of_read[cands[c].read_id] = c;
     b.n_work = (uint32_t)n_items;
     // planned records are written to a pinned staging buffer (one fast copy
     // each); the plan items live in the handle's scratch, reused across batches
     auto al256 = [](uint64_t x) { return (x + 255) & ~255ull; };
     const uint64_t n_cdesc = b.anchored ? n_cands : 0;
-    const uint64_t o_work = 0, o_sig = al256(o_work + sizeof(WorkDesc) * n_items);
-    const uint64_t o_plan = al256(o_sig + sizeof(SigDesc) * (uint64_t)n_cands);
-    const uint64_t o_cdesc = al256(o_plan + sizeof(PieceRef) * n_plan);
-    const uint64_t o_read = al256(o_cdesc + sizeof(CombineDesc) * n_cdesc);
-    const uint64_t stage_need = al256(o_read + sizeof(int) * (uint64_t)n_cands) + 256;
+    const uint64_t o_sig = 0, o_read = al256(o_sig + sizeof(SigDesc) * (uint64_t)n_cands);
+    const uint64_t o_cdesc = al256(o_read + sizeof(int) * (uint64_t)n_cands);
+    const uint64_t o_plan = al256(o_cdesc + sizeof(CombineDesc) * n_cdesc);
+    const uint64_t o_work = al256(o_plan + sizeof(PieceRef) * n_plan);
+    const uint64_t stage_need = al256(o_work + sizeof(WorkDesc) * n_items) + 256;
     if (h->stage_bytes < stage_need) {
         if (h->stage)
             cudaFreeHost(h->stage);
@@ -236,7 +231,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         h->stage_bytes = stage_need;
     }
     WorkDesc *work = (WorkDesc *)(h->stage + o_work);
-    SigDesc *sig_h = (SigDesc *)(h->stage + o_sig);
+    SigDesc *sig = (SigDesc *)(h->stage + o_sig);
     PieceRef *plan_h = (PieceRef *)(h->stage + o_plan);
     CombineDesc *cdesc_h = (CombineDesc *)(h->stage + o_cdesc);
     int *read_of = (int *)(h->stage + o_read);
@@ -247,25 +242,55 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     b.cells = 0;
     b.max_rows = 1;
     const int forced = h->cfg.kernel >= RA_KERNEL_VARIANT0 ? h->cfg.kernel - RA_KERNEL_VARIANT0 : -1;
-    int rc = over_parts([&](Part &pt_) {
+    rc = over_parts([&](Part &pt_) {
+        // alignments of one shape (rows, band) get one schedule: a small
+        // direct-mapped cache of choose_variant's answers (exact keys)
+        struct Choice {
+            int64_t n = -1, num = 0, den = 0, w = 0, m = 0;
+            int variant = 0;
+            Sched sc;
+        };
+        std::vector<Choice> cache(1024);
         auto schedule_item = [&](PlanItem &it, const BandDef &band, int64_t n) {
             Sched sc;
             if (b.plain || (forced >= 0 && forced < kNumVariants)) {
                 it.variant = b.plain ? 0 : forced;
                 sc = schedule(band, 0, n, kVariants[it.variant][0], kVariants[it.variant][1]);
             } else {
-                it.variant = choose_variant(band, 0, n, sc, h->slot_cost);
+                const uint64_t hk = ((uint64_t)n * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)band.m * 0xC2B2AE3D27D4EB4Full) ^
+                                    ((uint64_t)band.w * 0x165667B19E3779F9ull) ^ ((uint64_t)band.num << 17) ^
+                                    (uint64_t)band.den;
+                Choice &ch = cache[(hk ^ (hk >> 29)) & 1023];
+                if (ch.n == n && ch.m == band.m && ch.w == band.w && ch.num == band.num && ch.den == band.den) {
+                    it.variant = ch.variant;
+                    sc = ch.sc;
+                } else {
+                    it.variant = choose_variant(band, 0, n, sc, h->slot_cost);
+                    ch.n = n;
+                    ch.m = band.m;
+                    ch.w = band.w;
+                    ch.num = band.num;
+                    ch.den = band.den;
+                    ch.variant = it.variant;
+                    ch.sc = sc;
+                }
             }
             it.wave = 0;
             set_schedule(it, sc);
             pt_.max_rows = std::max<int>(pt_.max_rows, (int)n);
         };
-        uint64_t ix = pt_.ib, px = pt_.pb;
+        uint64_t ix = pt_.ib, px = pt_.pb, rx = pt_.rb;
         for (uint32_t c = pt_.c0; c < pt_.c1; ++c) {
             const rawalign_candidate_t &cd = cands[c];
             const int64_t n = (int64_t)(offs[cd.read_id + 1] - offs[cd.read_id]);
             const int64_t m = (int64_t)cd.ref_len_bases - k + 1;
-            const uint64_t r0 = sig[c].r_off;
+            const uint64_t r0 = rx;
+            rx += (uint64_t)m;
+            sig[c].ref_off = cd.ref_offset;
+            sig[c].r_off = r0;
+            sig[c].len = cd.ref_len_bases;
+            sig[c].strand = cd.strand;
+            read_of[c] = (int)cd.read_id;
             BandDef band;
             int32_t wrep;
             if (band_for(n, m, cd.band_w, cd.slope_num, cd.slope_den, band, wrep) != 0) {
@@ -335,19 +360,13 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     // launch order and classes (variant x ring size), longest first
     std::vector<int> &order = h->plan_order;
     b.classes.clear();
-    if (!make_classes(items, n_items, order, b.classes))
+    if (!make_classes(items, n_items, order, b.classes, h->plan_sort))
         return RA_EINVAL;
     if (b.plain)
         b.classes.clear();
     parallel_for(n_items, [&](uint64_t x0, uint64_t x1) {
         for (uint64_t x = x0; x < x1; ++x)
             work[x] = items[order[x]].wd;
-    });
-    parallel_for(n_cands, [&](uint64_t c0, uint64_t c1) {
-        for (uint64_t c = c0; c < c1; ++c) {
-            sig_h[c] = sig[c];
-            read_of[c] = (int)cands[c].read_id;
-        }
     });
     // device memory
     b.d_events = take<float>(h, b, b.n_events);
@@ -384,7 +403,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     // for them, and the host only for the copies themselves
     cudaStream_t s = h->upload;
     RA_CUDA(cudaMemcpyAsync(b.d_events, events, sizeof(float) * b.n_events, cudaMemcpyHostToDevice, s));
-    RA_CUDA(cudaMemcpyAsync(b.d_sig, sig_h, sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
+    RA_CUDA(cudaMemcpyAsync(b.d_sig, sig, sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_work, work, sizeof(WorkDesc) * b.n_work, cudaMemcpyHostToDevice, s));
     if (b.anchored && n_plan)
         RA_CUDA(cudaMemcpyAsync(b.d_plan, plan_h, sizeof(PieceRef) * n_plan, cudaMemcpyHostToDevice, s));

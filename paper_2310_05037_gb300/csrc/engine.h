@@ -256,6 +256,12 @@ struct PlanItem {
     double cost = 0;    // lane-steps: longest first
 };
 
+// Scratch of the launch-order sort, kept by a handle across batches.
+struct SortScratch {
+    std::vector<uint64_t> key, key2;
+    std::vector<int> tmp;
+};
+
 struct ServeState;
 
 }  // namespace ra_host
@@ -272,6 +278,7 @@ struct rawalign_dtw {
     size_t stage_bytes = 0;
     std::vector<ra_host::PlanItem> plan_items;  // planning scratch, reused across batches
     std::vector<int> plan_order;
+    ra_host::SortScratch plan_sort;
     cudaEvent_t fork = nullptr, join[kMaxClasses] = {};
     int device = 0;
     int sm_count = 152;
@@ -427,7 +434,8 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
 // resident blocks, or a ring in global memory) on everything else.  Classes
 // are returned longest-alignment first.  Returns false if more than
 // kMaxClasses would be needed.
-inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &order, std::vector<ClassLaunch> &classes)
+inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &order, std::vector<ClassLaunch> &classes,
+                         SortScratch &scr)
 {
     // Launch order: a stable LSD radix sort (16-bit digits) on one 64-bit key
     // per item, the bucket (variant, ring size, wave) above the complemented
@@ -444,15 +452,21 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
             ++i;
         return i;
     };
-    std::vector<uint64_t> key(n), key2(n);
-    std::vector<int> tmp(n);
-    order.resize(n);
+    if (scr.key.size() < n) {
+        scr.key.resize(n);
+        scr.key2.resize(n);
+        scr.tmp.resize(n);
+    }
+    if (order.size() < n)
+        order.resize(n);
+    uint64_t *key = scr.key.data(), *key2 = scr.key2.data();
+    int *ord = order.data(), *tmp = scr.tmp.data();
     parallel_for(n, [&](uint64_t lo, uint64_t hi) {
         for (uint64_t x = lo; x < hi; ++x) {
             const PlanItem &it = items[x];
             const uint64_t bucket = (uint64_t)((it.variant * kCaps + cap_index(it.cap)) * 2 + it.wave);
             key[x] = bucket << 32 | (uint64_t)~(uint32_t)std::max(it.wd.s_end, 0);
-            order[x] = (int)x;
+            ord[x] = (int)x;
         }
     });
     // each pass: per-chunk digit counts, offsets in (digit, chunk) order,
@@ -495,18 +509,20 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
             for (size_t x = n * t / T; x < n * (t + 1) / T; ++x) {
                 const uint32_t y = c[(key[x] >> shift) & 0xFFFF]++;
                 key2[y] = key[x];
-                tmp[y] = order[x];
+                tmp[y] = ord[x];
             }
         });
-        key.swap(key2);
-        order.swap(tmp);
+        std::swap(key, key2);
+        std::swap(ord, tmp);
     }
+    if (ord != order.data())
+        std::copy(ord, ord + n, order.data());
     // classes: runs of one (variant, ring size); a class's longest item heads
     // one of its two wave runs
     classes.clear();
     size_t pos = 0;
     while (pos < n) {
-        const PlanItem &f = items[order[pos]];
+        const PlanItem &f = items[ord[pos]];
         ClassLaunch cl;
         cl.G = kVariants[f.variant][0];
         cl.HR = kVariants[f.variant][1];
@@ -529,7 +545,10 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
 
 inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &order, std::vector<ClassLaunch> &classes)
 {
-    return make_classes(items.data(), items.size(), order, classes);
+    SortScratch scr;
+    const bool ok = make_classes(items.data(), items.size(), order, classes, scr);
+    order.resize(items.size());
+    return ok;
 }
 
 // Ring entries one piece needs: the stripe period plus two (written one step
