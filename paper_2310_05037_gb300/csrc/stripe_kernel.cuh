@@ -57,9 +57,26 @@ static __device__ __forceinline__ void st_shared_if(bool pred, float *addr, floa
                  :: "r"((int)pred), "r"(a), "f"(v) : "memory");
 }
 
+// Row-wise band DDA, r rows on: (Q0, R0) is floor and remainder of a band
+// edge at some row (0 <= R0 < den), (q1, r1) = divmod(num, den) the step per
+// row; (Q, R) receive the edge r rows further.  r <= 32, so the carry
+// floor((R0 + r r1) / den) is below 32 and found by a 5-bit binary search.
+static __device__ __forceinline__ void row_dda(int Q0, int R0, int q1, int r1, int den, int r, int &Q, int &R)
+{
+    const long long x = (long long)R0 + (long long)r * r1;
+    int c = 0;
+#pragma unroll
+    for (int bit = 16; bit >= 1; bit >>= 1)
+        if ((long long)(c + bit) * den <= x)
+            c += bit;
+    Q = Q0 + r * q1 + c;
+    R = (int)(x - (long long)c * den);
+}
+
 template <int G, int HR, bool FREE_END, bool RING_SMEM, bool ET>
 __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
 {
+    static_assert(HR < 32, "one bit of the band mask per row");
     constexpr int H = G * HR;
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int BIGROW = 1 << 29;
@@ -84,14 +101,10 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
     int m = 1, s = 0, s_end = 0;
     int k = 0, j = 0, b = INT_MAX;
     float e[HR], D[HR];
-    int lo[HR];
-    unsigned wid[HR];
 #pragma unroll
     for (int r = 0; r < HR; ++r) {
         e[r] = 0.f;
         D[r] = kInf;
-        lo[r] = kBigCol;
-        wid[r] = 0;
     }
     // column-wise DDA: rows in band at column j are [Aq, Bq]
     // relative to the lane's first row
@@ -105,11 +118,13 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
     int bestj = -1;
     int lastLo = kBigCol, r_last = 0;
     float rowmin = kInf;  // early termination: smallest value of the stripe's last row so far
+    unsigned ncells = 0;  // in-band cells since the last flush to lc->cells
     unsigned lastWid = 0;
     bool done = true, exhausted = false, have = false;
 
-    // set-up of this lane's rows for stripe k (row-wise band DDA from the
-    // lane's first row, kept in shared memory).  The DP column and the
+    // set-up of this lane's rows for stripe k: its events, and its last
+    // column from the row-wise band DDA of its first row (kept in shared
+    // memory), advanced to its last row in O(1).  The DP column and the
     // diagonal are not reset: a lane enters a stripe at least one column
     // before the first in-band column of its rows (the period dC guarantees
     // it), so its first step there has every row out of band, d = +inf, and
@@ -119,45 +134,21 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         const float *ev = gc->ev;
         const int i0 = k * H + t * HR;
         const int loQ = lc->loQ, loR = lc->loR, hiQ = lc->hiQ, hiR = lc->hiR;
-        int Ql = loQ, Rl = loR, Qh = hiQ, Rh = hiR;
-        unsigned long long cells = 0;
         b = -1;
         nvalid = min(max(nrows - i0, 0), HR);
 #pragma unroll
         for (int r = 0; r < HR; ++r) {
             const int li = i0 + r;
-            if (li < nrows) {
-                int l = Ql + (Rl > 0 ? 1 : 0);
-                l = l < 0 ? 0 : l;
-                const int hh = Qh < m - 1 ? Qh : m - 1;
-                if (hh >= l) {
-                    lo[r] = l;
-                    wid[r] = (unsigned)(hh - l);
-                    cells += (unsigned long long)(hh - l + 1);
-                } else {
-                    lo[r] = kBigCol;
-                    wid[r] = 0;
-                }
-                b = hh;
+            if (li < nrows)
                 e[r] = __ldg(ev + li);
-            } else {
-                lo[r] = kBigCol;
-                wid[r] = 0;
-            }
-            Ql += q1;
-            Rl += r1;
-            if (Rl >= den) {
-                Ql += 1;
-                Rl -= den;
-            }
-            Qh += q1;
-            Rh += r1;
-            if (Rh >= den) {
-                Qh += 1;
-                Rh -= den;
-            }
         }
-        lc->cells += cells;
+        // the lane leaves the stripe after the band end of its last row
+        // (clamped to the table); its in-band cells are counted per step
+        if (nvalid > 0) {
+            int Qh, Rh;
+            row_dda(hiQ, hiR, q1, r1, den, nvalid - 1, Qh, Rh);
+            b = Qh < m - 1 ? Qh : m - 1;
+        }
         if (i0 != 0) {
             int Qa = loQ - q1, Ra = loR - r1;
             if (Ra < 0) {
@@ -186,14 +177,14 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
             rowmin = kInf;
         if (FREE_END && holds_last) {
             r_last = gc->r_last;
-            lastLo = kBigCol;
-            lastWid = 0;
-#pragma unroll
-            for (int r = 0; r < HR; ++r)
-                if (r == r_last) {
-                    lastLo = lo[r];
-                    lastWid = wid[r];
-                }
+            int Ql, Rl, Qh, Rh;
+            row_dda(loQ, loR, q1, r1, den, r_last, Ql, Rl);
+            row_dda(hiQ, hiR, q1, r1, den, r_last, Qh, Rh);
+            int l = Ql + (Rl > 0 ? 1 : 0);
+            l = l < 0 ? 0 : l;
+            const int hh = Qh < m - 1 ? Qh : m - 1;
+            lastLo = hh >= l ? l : kBigCol;
+            lastWid = hh >= l ? (unsigned)(hh - l) : 0u;
         }
     };
 
@@ -204,9 +195,6 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         holds_last = false;
         nvalid = 0;
         colmax = -1;
-#pragma unroll
-        for (int r = 0; r < HR; ++r)
-            lo[r] = kBigCol;
     };
 
     lc->cells = 0;
@@ -370,8 +358,10 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
 
         // steps until the first group of this warp finishes its alignment
         const int rem = done ? INT_MAX : s_end - s;
-        // (early termination: at most 64 steps, then the group checks its abort flag)
-        const int nstep = __reduce_min_sync(FULL, ET ? min(rem, 64) : rem);
+        // (early termination: at most 64 steps, then the group checks its
+        // abort flag; otherwise at most 2^27 steps, so that the lane's cell
+        // count, at most HR < 32 per step, fits in 32 bits until it is flushed)
+        const int nstep = __reduce_min_sync(FULL, ET ? min(rem, 64) : min(rem, 1 << 27));
 #pragma unroll 2
         for (int q = 0; q < nstep; ++q) {
             ++j;
@@ -503,6 +493,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                 unsigned M;
                 asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(M) : "r"(loN), "r"(width));
                 M = ((unsigned)j <= (unsigned)colmax) ? M : 0u;
+                ncells += __popc(M);
 #pragma unroll
                 for (int r = 0; r < HR; ++r)
                     eg[r] = ((M >> r) & 1u) ? e[r] : kInf;
@@ -539,6 +530,8 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
             __syncwarp();
         }
         s += nstep;
+        lc->cells += ncells;
+        ncells = 0;
         if (!done && s == s_end)
             done = true;
         if (ET) {
