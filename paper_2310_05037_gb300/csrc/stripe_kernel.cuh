@@ -538,8 +538,8 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
             __syncwarp();
             if (!done && gc->abort && !gc->written) {
                 // pruned: the cost bound and the score bound take the result's
-                // place, flagged; the cells of the started stripes are added at
-                // the next acquisition
+                // place, flagged; the cells computed so far are added at the
+                // next acquisition
                 done = true;
                 if (t == 0) {
                     rawalign_result_t *o = p.results + gc->cand;
