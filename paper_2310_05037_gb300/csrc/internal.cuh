@@ -108,4 +108,20 @@ cudaError_t launch_combine(const CombineDesc *d, int n, const PieceRef *plan, co
 cudaError_t launch_decide(rawalign_result_t *results, int n, const unsigned long long *best_keys,
                           const int *read_of, float thr, int final_decision, cudaStream_t s);
 
+// Row-wise band DDA, r rows on: (Q0, R0) is floor and remainder of a band
+// edge at some row (0 <= R0 < den), (q1, r1) = divmod(num, den) the step per
+// row; (Q, R) receive the edge r rows further.  For r < 32 the carry
+// floor((R0 + r r1) / den) is at most r, so a 5-bit binary search finds it.
+__host__ __device__ __forceinline__ void row_dda(int Q0, int R0, int q1, int r1, int den, int r, int &Q, int &R)
+{
+    const long long x = (long long)R0 + (long long)r * r1;
+    int c = 0;
+#pragma unroll
+    for (int bit = 16; bit >= 1; bit >>= 1)
+        if ((long long)(c + bit) * den <= x)
+            c += bit;
+    Q = Q0 + r * q1 + c;
+    R = (int)(x - (long long)c * den);
+}
+
 }  // namespace ra

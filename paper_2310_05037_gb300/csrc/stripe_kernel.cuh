@@ -57,22 +57,6 @@ static __device__ __forceinline__ void st_shared_if(bool pred, float *addr, floa
                  :: "r"((int)pred), "r"(a), "f"(v) : "memory");
 }
 
-// Row-wise band DDA, r rows on: (Q0, R0) is floor and remainder of a band
-// edge at some row (0 <= R0 < den), (q1, r1) = divmod(num, den) the step per
-// row; (Q, R) receive the edge r rows further.  r <= 32, so the carry
-// floor((R0 + r r1) / den) is below 32 and found by a 5-bit binary search.
-static __device__ __forceinline__ void row_dda(int Q0, int R0, int q1, int r1, int den, int r, int &Q, int &R)
-{
-    const long long x = (long long)R0 + (long long)r * r1;
-    int c = 0;
-#pragma unroll
-    for (int bit = 16; bit >= 1; bit >>= 1)
-        if ((long long)(c + bit) * den <= x)
-            c += bit;
-    Q = Q0 + r * q1 + c;
-    R = (int)(x - (long long)c * den);
-}
-
 template <int G, int HR, bool FREE_END, bool RING_SMEM, bool ET>
 __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
 {

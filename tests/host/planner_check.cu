@@ -10,7 +10,10 @@
 //   - the lane holding the last row leaves it within s_end steps.
 // It also checks make_classes: classes are runs of one variant and ring
 // size, longest first inside a class (first candidates before the others),
-// classes ordered by their longest alignment.
+// classes ordered by their longest alignment; and the O(1) row step of the
+// band DDA (ra::row_dda, used by the kernel at every stripe change) against
+// stepping row by row.
+#include <cstdint>
 #include <cstdio>
 #include <random>
 
@@ -125,6 +128,30 @@ int main()
             check_schedule(band, n, kVariants[v][0], kVariants[v][1], steps);
             ++cases;
         }
+    }
+    // O(1) row step of the band DDA against r single steps
+    for (int rep = 0; rep < 200000; ++rep) {
+        const int den = 1 + (int)(rng() % (rep % 3 == 0 ? 7 : (1u << 30) - 1));
+        const int64_t num = (int64_t)(rng() % (rep % 2 ? 4ull * den : (1ull << 30)));
+        const int q1 = (int)(num / den), r1 = (int)(num % den);
+        const int Q0 = (int)(rng() % 2000000) - 1000000, R0 = (int)(rng() % den);
+        const int r = (int)(rng() % 32);
+        int64_t Q = Q0, R = R0;
+        for (int x = 0; x < r; ++x) {
+            Q += q1;
+            R += r1;
+            if (R >= den) {
+                Q += 1;
+                R -= den;
+            }
+        }
+        if (Q > INT32_MAX)
+            continue;  // not a band edge: columns stay below 2^31
+        int Qf, Rf;
+        ra::row_dda(Q0, R0, q1, r1, den, r, Qf, Rf);
+        CHECK(Qf == Q && Rf == R, "row_dda den %d num %lld r %d: %d/%d vs %lld/%lld\n", den, (long long)num, r, Qf,
+              Rf, (long long)Q, (long long)R);
+        ++cases;
     }
     // launch classes
     for (int rep = 0; rep < 50; ++rep) {
