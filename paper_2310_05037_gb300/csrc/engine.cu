@@ -109,8 +109,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         int max_rows = 1;
         int rc = RA_OK;
     };
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const uint32_t n_parts = std::max<uint32_t>(1, std::min<uint32_t>(std::min(hw, 16u), (n_cands + 4095) / 4096));
+    const uint32_t n_parts = std::max<uint32_t>(1, std::min<uint32_t>(host_threads(), (n_cands + 4095) / 4096));
     std::vector<Part> parts(n_parts);
     for (uint32_t t = 0; t < n_parts; ++t) {
         parts[t].c0 = (uint32_t)((uint64_t)n_cands * t / n_parts);
@@ -350,10 +349,11 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         return rc;
     for (auto &pt_ : parts)
         b.max_rows = std::max(b.max_rows, pt_.max_rows);
-    if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO)
-        shorten_longest(items, n_items, h->sm_count, h->slot_cost);
     uint64_t slots[kNumVariants];
-    variant_slots(items, n_items, slots);
+    if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO)
+        shorten_longest(items, n_items, h->sm_count, h->slot_cost, slots);
+    else
+        variant_slots(items, n_items, slots);
     b.slots = 0;
     for (int v = 0; v < kNumVariants; ++v)
         b.slots += slots[v];

@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -35,21 +37,120 @@ constexpr int kNumVariants = 10;
 constexpr int kMaxClasses = 64;              // launches per run (variant x ring size)
 constexpr size_t kSmemRingLimit = 96 * 1024; // larger rings go to global memory
 
-// Runs fn(lo, hi) over [0, n) on up to 16 host threads (one when n is small).
+// Host worker threads for the planner's parallel loops, created once per
+// process.  One loop runs on the pool at a time; a loop started while the
+// pool is busy (another handle planning on another thread, or a loop inside
+// a pool task) runs on threads of its own instead.  The calling thread takes
+// tasks too, so a loop also completes if the workers are gone (a forked child).
+class WorkerPool {
+public:
+    explicit WorkerPool(unsigned workers)
+    {
+        for (unsigned w = 0; w < workers; ++w)
+            th_.emplace_back([this] { work(); });
+    }
+    ~WorkerPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : th_)
+            t.join();
+    }
+    // Runs fn(t) for t in [0, T); false (nothing run) if the pool is busy.
+    bool try_run(unsigned T, const std::function<void(unsigned)> &fn)
+    {
+        std::unique_lock<std::mutex> rl(run_mu_, std::try_to_lock);
+        if (!rl.owns_lock())
+            return false;
+        std::unique_lock<std::mutex> lk(mu_);
+        job_ = &fn;
+        tasks_ = T;
+        next_ = 0;
+        pending_ = T;
+        ++gen_;
+        cv_.notify_all();
+        take(lk);
+        done_cv_.wait(lk, [&] { return pending_ == 0; });
+        job_ = nullptr;
+        return true;
+    }
+
+private:
+    void take(std::unique_lock<std::mutex> &lk)
+    {
+        while (job_ && next_ < tasks_) {
+            const unsigned t = next_++;
+            const std::function<void(unsigned)> *job = job_;
+            lk.unlock();
+            (*job)(t);
+            lk.lock();
+            if (--pending_ == 0)
+                done_cv_.notify_all();
+        }
+    }
+    void work()
+    {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        while (true) {
+            cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+            if (stop_)
+                return;
+            seen = gen_;
+            take(lk);
+        }
+    }
+    std::mutex run_mu_, mu_;
+    std::condition_variable cv_, done_cv_;
+    std::vector<std::thread> th_;
+    const std::function<void(unsigned)> *job_ = nullptr;
+    unsigned tasks_ = 0, next_ = 0, pending_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+inline unsigned host_threads()
+{
+    return std::min(std::max(1u, std::thread::hardware_concurrency()), 16u);
+}
+
+inline WorkerPool &worker_pool()
+{
+    static WorkerPool pool(host_threads() - 1);
+    return pool;
+}
+
+// Runs task(t) for t in [0, T) on the worker pool (or on threads of its own
+// when the pool is busy).
+inline void run_tasks(unsigned T, const std::function<void(unsigned)> &task)
+{
+    if (T <= 1) {
+        if (T == 1)
+            task(0);
+        return;
+    }
+    if (worker_pool().try_run(T, task))
+        return;
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < T; ++t)
+        th.emplace_back(task, t);
+    for (auto &x : th)
+        x.join();
+}
+
+// Runs fn(lo, hi) over [0, n) in up to 16 ranges (one when n is small).
 template <typename F>
 inline void parallel_for(uint64_t n, F fn, uint64_t min_per_thread = 1 << 15)
 {
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const uint64_t T = std::max<uint64_t>(1, std::min<uint64_t>(std::min(hw, 16u), n / min_per_thread));
+    const uint64_t T = std::max<uint64_t>(1, std::min<uint64_t>(host_threads(), n / min_per_thread));
     if (T == 1) {
         fn((uint64_t)0, n);
         return;
     }
-    std::vector<std::thread> th;
-    for (uint64_t t = 0; t < T; ++t)
-        th.emplace_back(fn, n * t / T, n * (t + 1) / T);
-    for (auto &x : th)
-        x.join();
+    run_tasks((unsigned)T, [&](unsigned t) { fn(n * t / T, n * (t + 1) / T); });
 }
 
 // ---------------------------------------------------------------- band math
@@ -384,9 +485,9 @@ inline void variant_slots(const PlanItem *items, size_t n, uint64_t out[kNumVari
     });
 }
 
-inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const double *cost)
+// slots: receives the lane-cell slots per variant after the pass.
+inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const double *cost, uint64_t slots[kNumVariants])
 {
-    uint64_t slots[kNumVariants];
     variant_slots(items, n, slots);
     double total = 0;
     for (int v = 0; v < kNumVariants; ++v)
@@ -394,7 +495,10 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
     const double groups = 32.0 * std::max(sm_count, 1);
     const double theta = (double)n < 4.0 * groups ? 0.5 : 1.0;
     const double batch_len = theta * total / (512.0 * std::max(sm_count, 1));
+    std::mutex mu;
     parallel_for(n, [&](uint64_t lo, uint64_t hi) {
+        int64_t moved[kNumVariants] = {};
+        bool any = false;
         for (uint64_t x = lo; x < hi; ++x) {
             PlanItem &it = items[x];
             const int v0 = it.variant;
@@ -422,8 +526,16 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
             }
             if (best < 0 || (double)best_s.s_end * kVariants[best][1] * cost[best] >= dur)
                 continue;
+            moved[v0] -= (int64_t)it.wd.s_end * kVariants[v0][0] * kVariants[v0][1];
             it.variant = best;
             set_schedule(it, best_s);
+            moved[best] += (int64_t)std::max(it.wd.s_end, 0) * kVariants[best][0] * kVariants[best][1];
+            any = true;
+        }
+        if (any) {
+            std::lock_guard<std::mutex> g(mu);
+            for (int v = 0; v < kNumVariants; ++v)
+                slots[v] = (uint64_t)((int64_t)slots[v] + moved[v]);
         }
     });
 }
@@ -471,20 +583,9 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
     });
     // each pass: per-chunk digit counts, offsets in (digit, chunk) order,
     // then every chunk scatters its items in order (stable)
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const size_t T = std::max<size_t>(1, std::min<size_t>(std::min(hw, 16u), n / (1 << 16)));
-    std::vector<uint32_t> cnt(T << 16);
-    auto chunks = [&](auto fn) {
-        if (T == 1) {
-            fn((size_t)0);
-            return;
-        }
-        std::vector<std::thread> th;
-        for (size_t t = 0; t < T; ++t)
-            th.emplace_back(fn, t);
-        for (auto &x : th)
-            x.join();
-    };
+    const size_t T = std::max<size_t>(1, std::min<size_t>(host_threads(), n / (1 << 16)));
+    std::vector<uint32_t> cnt(T << 16), tot(1 << 16);
+    auto chunks = [&](auto fn) { run_tasks((unsigned)T, [&](unsigned t) { fn((size_t)t); }); };
     for (int shift = 0; shift < 48 && n > 1; shift += 16) {
         chunks([&](size_t t) {
             uint32_t *c = cnt.data() + (t << 16);
@@ -497,13 +598,32 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
             first_digit += cnt[(t << 16) + ((key[0] >> shift) & 0xFFFF)];
         if (first_digit == n)
             continue;  // one value of this digit: the pass would move nothing
-        uint32_t acc = 0;
-        for (size_t d = 0; d < (1 << 16); ++d)
-            for (size_t t = 0; t < T; ++t) {
-                const uint32_t c = cnt[(t << 16) + d];
-                cnt[(t << 16) + d] = acc;
-                acc += c;
+        // offsets in (digit, chunk) order: each digit's total over the
+        // chunks, an exclusive scan of the totals, then each digit's chunks
+        chunks([&](size_t t) {
+            for (size_t d = (t << 16) / T; d < ((t + 1) << 16) / T; ++d) {
+                uint32_t sum = 0;
+                for (size_t c = 0; c < T; ++c)
+                    sum += cnt[(c << 16) + d];
+                tot[d] = sum;
             }
+        });
+        uint32_t acc = 0;
+        for (size_t d = 0; d < (1 << 16); ++d) {
+            const uint32_t c = tot[d];
+            tot[d] = acc;
+            acc += c;
+        }
+        chunks([&](size_t t) {
+            for (size_t d = (t << 16) / T; d < ((t + 1) << 16) / T; ++d) {
+                uint32_t at = tot[d];
+                for (size_t c = 0; c < T; ++c) {
+                    const uint32_t v = cnt[(c << 16) + d];
+                    cnt[(c << 16) + d] = at;
+                    at += v;
+                }
+            }
+        });
         chunks([&](size_t t) {
             uint32_t *c = cnt.data() + (t << 16);
             for (size_t x = n * t / T; x < n * (t + 1) / T; ++x) {

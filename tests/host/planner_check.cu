@@ -12,10 +12,14 @@
 // size, longest first inside a class (first candidates before the others),
 // classes ordered by their longest alignment; and the O(1) row step of the
 // band DDA (ra::row_dda, used by the kernel at every stripe change) against
-// stepping row by row.
+// stepping row by row; and that the planner's parallel loops visit every
+// index once, with concurrent and nested callers.
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <random>
+#include <thread>
+#include <vector>
 
 #include "engine.h"
 
@@ -128,6 +132,40 @@ int main()
             check_schedule(band, n, kVariants[v][0], kVariants[v][1], steps);
             ++cases;
         }
+    }
+    // the planner's parallel loops: every index once, also with two callers
+    // at a time (one falls back to threads of its own) and nested loops
+    {
+        auto sum_loop = [](uint64_t n, bool nested) {
+            std::vector<std::atomic<uint32_t>> hit(n);
+            for (auto &h : hit)
+                h = 0;
+            parallel_for(n, [&](uint64_t lo, uint64_t hi) {
+                if (nested)
+                    parallel_for(hi - lo, [&](uint64_t a, uint64_t b) {
+                        for (uint64_t x = lo + a; x < lo + b; ++x)
+                            hit[x]++;
+                    }, 1 << 10);
+                else
+                    for (uint64_t x = lo; x < hi; ++x)
+                        hit[x]++;
+            }, 1 << 12);
+            for (auto &h : hit)
+                if (h != 1)
+                    return false;
+            return true;
+        };
+        std::atomic<int> bad{0};
+        std::vector<std::thread> callers;
+        for (int c = 0; c < 3; ++c)
+            callers.emplace_back([&, c] {
+                for (int rep = 0; rep < 40; ++rep)
+                    if (!sum_loop(1000 + 7919 * (uint64_t)(rep + c), (rep + c) % 3 == 0))
+                        bad++;
+            });
+        for (auto &t : callers)
+            t.join();
+        CHECK(bad == 0, "parallel_for missed or repeated indices (%d loops)\n", (int)bad);
     }
     // O(1) row step of the band DDA against r single steps
     for (int rep = 0; rep < 200000; ++rep) {

@@ -10,7 +10,7 @@ torch = pytest.importorskip("torch")
 from paper_2310_05037_gb300 import binding as B  # noqa: E402
 from paper_2310_05037_gb300 import synth as S  # noqa: E402
 
-from gpu_util import assert_bit_exact, edge_workload, run_gpu, run_oracle, tiny_workload  # noqa: E402
+from gpu_util import arena_bytes_for, assert_bit_exact, edge_workload, run_gpu, run_oracle, tiny_workload  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +63,25 @@ def test_graph_replays_match_and_repeat():
     ora = run_oracle(w)
     for o in outs:
         assert_bit_exact(o, ora)
+
+
+def test_batch_stats():
+    """Counters of a run: the batch's cells are the results' cells, the plan's
+    lane-cell slots cover them, and the timed parts are positive."""
+    w = S.scaled("batched", "small")
+    al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena_bytes_for(w), k=w.k, b_match=w.b_match,
+                   score_threshold=w.score_threshold, end_mode=w.end_mode)
+    try:
+        b = al.prepare(w.events, w.read_offsets, w.cands)
+        r = al.poll(al.run(b), w.n_cands)
+        st = al.stats(b)
+        assert st.cells == int(r["cells"].sum())
+        assert st.slots >= st.cells > 0
+        assert st.launches >= 3
+        assert 0 < st.dtw_ms <= st.total_ms
+        al.release(b)
+    finally:
+        al.close()
 
 
 def test_fp64_agreement():
