@@ -1,8 +1,9 @@
 """Host-side planner checks (no GPU): compiles tests/host/planner_check.cu
 against the library's planning header and runs it.  It replays the striped
 kernel's lane schedule for random bands and every variant and verifies the
-period, ring size and step count the planner computes in closed form, and
-the launch-class ordering."""
+period, ring size and step count the planner computes in closed form, the
+launch-class ordering, the kernel's O(1) row step of the band DDA, and the
+host worker pool's parallel loops."""
 import os
 import shutil
 import subprocess
