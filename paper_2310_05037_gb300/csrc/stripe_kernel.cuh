@@ -90,9 +90,11 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         e[r] = 0.f;
         D[r] = kInf;
     }
-    // column-wise DDA: rows in band at column j are [Aq, Bq]
-    // relative to the lane's first row
-    int Bq = -BIGROW, Br = 0, Aq = BIGROW, Ar = 0, cq = 0, cr = 0, cnum = 1;
+    // column-wise DDA: rows in band at column j are [Aq, Bq] relative to
+    // the lane's first row.  Only Bq (floor, remainder Br) is stepped: both
+    // edges advance by the same (cq, cr) per column, so the lower edge is the
+    // upper one less a constant (Dq, Dr), Aq = Bq - Dq - [Br < Dr]
+    int Bq = -BIGROW, Br = 0, Dq = -2 * BIGROW, Dr = 0, cq = 0, cr = 0, cnum = 1;
     int nvalid = 0, colmax = -1;
     int loA = kBigCol;
     unsigned widA = 0;
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                         k = 0;
                         j = wd.a0 - 1 - t;  // first column of this lane
                         {
+                            int Aq, Ar;
                             if (num == 0) {
                                 Bq = BIGROW;
                                 Aq = -BIGROW;
@@ -310,6 +313,12 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                             if (Ar < 0) {
                                 Aq -= 1;
                                 Ar += cnum;
+                            }
+                            Dq = Bq - Aq;
+                            Dr = Br - Ar;
+                            if (Dr < 0) {
+                                Dr += cnum;
+                                Dq -= 1;
                             }
                         }
                         --j;
@@ -355,12 +364,6 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                 if (Br >= cnum) {
                     Bq += 1;
                     Br -= cnum;
-                }
-                Aq += cq;
-                Ar += cr;
-                if (Ar >= cnum) {
-                    Aq += 1;
-                    Ar -= cnum;
                 }
             }
             if (j > b) {
@@ -441,12 +444,6 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                             Bq -= 1;
                             Br += cnum;
                         }
-                        Aq -= H + qdC;
-                        Ar -= rdC;
-                        if (Ar < 0) {
-                            Aq -= 1;
-                            Ar += cnum;
-                        }
                     }
                 } else {
                     finish_lane();
@@ -471,6 +468,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
             float eg[HR];
             {
                 // rows [loN, hiN) are in band: one bit-field mask instruction
+                const int Aq = Bq - Dq - (Br < Dr ? 1 : 0);
                 const int loN = max(Aq, 0);
                 const int hiN = min(Bq + 1, nvalid);
                 const int width = max(hiN - loN, 0);
