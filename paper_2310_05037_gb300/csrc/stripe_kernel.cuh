@@ -21,9 +21,12 @@
 // current column is replaced by +inf, so d = |e - r| = +inf and the cell is
 // +inf whatever its neighbours are; this keeps the select off the dependent
 // min -> add chain.  The rows in band at column j form an interval, found
-// each step by two column-wise DDAs (first row whose band starts after j,
-// first row whose band ends before j) and turned into a bit mask by one
-// bmsk instruction.
+// each step by a column-wise DDA (the last row whose band reaches j; the
+// first row whose band has started is that one less a constant) and turned
+// into a bit mask by one bmsk instruction.  The population count of the
+// mask is the lane's in-band cells of the step, so the stripe change, which
+// each lane makes alone while the rest of its warp waits, only loads the
+// lane's events and finds its last column in O(1).
 // The cell itself is sub, min3 (one exact 3-input min), add, in that order.
 #pragma once
 
