@@ -15,8 +15,11 @@ Prints one JSON line (rank 0).  value = in-band DTW cells / device time
 (GCUPS, whole job over all ranks).  e2e = the same metric through the public
 submit/poll calls from pinned host buffers (copies included).  Extra keys:
 reads_per_s, the plain one-alignment-per-launch kernel on a sample of the same
-workload, and the batched/plain speed-up.  --impl reference times the CPU
-oracle (the only reference this path has) on a bounded sample.
+workload, the batched/plain speed-up, the Read-Until serving loop, and
+"workloads": the Read-Until prefix, long-read and anchor-guided batches at
+full size, each with device GCUPS, its fraction of the roofline and its
+end-to-end rate (--extra picks them).  --impl reference times the CPU oracle
+(the only reference this path has) on a bounded sample.
 """
 from __future__ import annotations
 
@@ -24,8 +27,10 @@ import argparse
 import json
 import os
 import statistics
+import platform
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -54,6 +59,14 @@ WORKLOADS = {
 }
 METRIC = "DTW GCUPS and reads/s (batched and served vs plain per-alignment kernel); p50/p99 chunk latency"
 OPS_PER_CELL = 4  # sub, min, min, add per DP cell
+# ALU-pipe lane-slots per in-band cell of the striped kernel's hot loop: the
+# 3-input min (issued at half rate: 2 slots) and the band-mask bit test and
+# select (1 + 1); the subtraction and the addition go to the FMA pipe.
+ALU_SLOTS_PER_CELL = 4.0
+# DRAM bytes (read + write) of the DTW part of one step of a workload, from an
+# ncu capture of the current kernel (None: not captured for this kernel).
+TRAFFIC = {}
+TRAFFIC_BASIS = ""
 
 
 def load_peaks():
@@ -73,12 +86,12 @@ class ClockSampler:
     def __init__(self, gpu_index=0):
         self.gpu = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix="rawalign_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
@@ -94,11 +107,17 @@ class ClockSampler:
             except Exception:
                 self.p.kill()
             self.f.close()
+        self.rows = self._read()
+        if self.path:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
 
-    def summary(self):
-        if not self.p:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    def _read(self):
         rows = []
+        if not self.p or not self.path:
+            return rows
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
@@ -107,6 +126,12 @@ class ClockSampler:
                 rows.append((float(f[1]), float(f[2]), float(f[3]), f[4], f[5], f[6], f[7], f[8]))
             except ValueError:
                 continue
+        return rows
+
+    def summary(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = self.rows
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         pmax = max(r[2] for r in rows)
@@ -188,16 +213,183 @@ def cpu_baseline(w, seconds=15.0, seed=1):
                       % (done, cells, el), "seconds": el}
 
 
-def workload_name(args):
-    d = WORKLOADS[args.workload]
-    return d % args.reads if args.workload in ("batched", "batched_et") else d
+def host_cpu():
+    """Model name and online cores of the host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"cpu_model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "nproc": os.cpu_count()}
 
 
-def make_workload(S, args, rank):
+def workload_name(args, name=None):
+    name = name or args.workload
+    d = WORKLOADS[name]
+    return d % args.reads if name in ("batched", "batched_et") else d
+
+
+def make_workload(S, args, rank, name=None):
     """The step's batch; every rank draws its own (weak scaling, replicas)."""
-    if args.workload in ("batched", "batched_et"):
-        return S.config_batched(n_reads=args.reads, seed=0x5EED0002 + rank, true_first=args.workload == "batched_et")
-    return S.scaled(args.workload, "full", seed=None if rank == 0 else 0x5EED1000 + rank)
+    name = name or args.workload
+    if name in ("batched", "batched_et"):
+        return S.config_batched(n_reads=args.reads, seed=0x5EED0002 + rank, true_first=name == "batched_et")
+    return S.scaled(name, "full", seed=None if rank == 0 else 0x5EED1000 + rank)
+
+
+def arena_bytes(B, w):
+    """The prepared batch and two submissions in flight, plus ring scratch
+    for bands too wide for shared-memory rings."""
+    m_total = int(np.sum(w.cands["ref_len_bases"].astype(np.int64) - w.k + 1))
+    need = B.rawalign_dtw_batch_bytes(len(w.events), w.n_reads, w.n_cands, m_total)
+    arena = 3 * need + len(w.ref2bit) + (256 << 20)
+    if w.anchor_offsets is not None:  # per-gap work items and results, pieces
+        arena += 3 * (len(w.anchors) + w.n_cands) * 512
+    m_c = w.cands["ref_len_bases"].astype(np.int64) - w.k + 1
+    w_c = np.where(w.cands["band_w"] < 0, m_c, w.cands["band_w"].astype(np.int64))
+    if w.n_cands and int(np.max(2 * w_c + 1)) > 2000:
+        arena += 3 * (2 << 30)
+    return arena, m_total
+
+
+def prepare(al, w):
+    if w.anchor_offsets is not None:
+        return al.prepare_anchored(w.events, w.read_offsets, w.cands, w.anchors, w.anchor_offsets)
+    return al.prepare(w.events, w.read_offsets, w.cands)
+
+
+def time_resident(torch, al, batch, w, steps, warmup, flush, clk_ctx=None):
+    """Replays of the prepared batch (inputs resident in HBM), CUDA events on
+    the library's stream around each step, L2 flushed before each step.
+    Returns per-step results, device times and the DTW part's times."""
+    stream = al.stream
+    res = None
+    for _ in range(warmup):
+        res = al.poll(al.run(batch), w.n_cands)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    dtw_ms, tot_ms = [], []
+    torch.cuda.synchronize()
+    with (clk_ctx if clk_ctx is not None else _Null()):
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev0[i].record(stream)
+            t = al.run(batch)
+            with torch.cuda.stream(stream):
+                ev1[i].record(stream)
+            al.poll(t, 0)
+            dtw_ms.append(al.stats(batch).dtw_ms)
+            tot_ms.append(ev0[i].elapsed_time(ev1[i]))
+        torch.cuda.synchronize()
+    return res, tot_ms, dtw_ms
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def time_e2e(B, torch, al, w, steps, world):
+    """The same cells through the public submit/poll calls from pinned host
+    buffers: inputs copied in and results copied out every step, two
+    submissions in flight (step i+1 planned and uploaded while step i runs)."""
+    from paper_2310_05037_gb300 import synth as S
+
+    anchored = w.anchor_offsets is not None
+    ev_np = torch.from_numpy(w.events).pin_memory().numpy()
+    off_np = torch.from_numpy(w.read_offsets.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    cand_np = torch.from_numpy(w.cands.view(np.uint8)).pin_memory().numpy().view(S.CANDIDATE_DTYPE)
+
+    def submit():
+        if anchored:
+            return B.rawalign_dtw_submit_anchored(al.h, ev_np, off_np, cand_np, w.anchors, w.anchor_offsets)
+        return B.rawalign_dtw_submit_batch(al.h, ev_np, off_np, cand_np)
+
+    def pipelined(k):
+        t = submit()
+        r = None
+        for i in range(k):
+            t_next = submit() if i + 1 < k else None
+            r = B.rawalign_dtw_poll(al.h, t, w.n_cands)
+            t = t_next
+        return r
+
+    pipelined(2)
+    barrier(world)
+    t0 = time.perf_counter()
+    r = pipelined(steps)
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    cells = sum_over_ranks(float(r["cells"].sum()) * steps, world)
+    return {"value": round(cells / el / 1e9, 2), "unit": "GCUPS",
+            "h2d_bytes_per_step": int(w.events.nbytes + w.read_offsets.nbytes + w.cands.nbytes +
+                                      (w.anchors.nbytes + w.anchor_offsets.nbytes if anchored else 0)),
+            "d2h_bytes_per_step": int(w.n_cands * B.RESULT_DTYPE.itemsize),
+            "ms_per_step": round(el / steps * 1e3, 2),
+            "pipelining": "two submissions in flight (submit i+1, then poll i)"}
+
+
+def peak_gcups(torch, local):
+    peaks = load_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", 2070.0))
+    return sms, f_max, sms * 128 * f_max * 1e6 / OPS_PER_CELL / 1e9
+
+
+def pipe_bound_gcups(sms, f_mhz):
+    """Bound of the ALU pipe for the striped kernel's instruction mix:
+    SMs x 64 ALU lanes per clock x f / ALU lane-slots per cell."""
+    return sms * 64 * f_mhz * 1e6 / ALU_SLOTS_PER_CELL / 1e9
+
+
+def measure_extra(B, S, torch, args, name, local, flush, peak):
+    """One more full-size workload: device GCUPS of resident replays, the DTW
+    part's fraction of the roofline, and end to end through submit/poll."""
+    t0 = time.perf_counter()
+    w = make_workload(S, args, 0, name)
+    gen_s = time.perf_counter() - t0
+    arena, m_total = arena_bytes(B, w)
+    al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena, device="cuda:%d" % local)
+    try:
+        batch = prepare(al, w)
+        steps = max(3, min(args.steps, 5))
+        res, tot_ms, dtw_ms = time_resident(torch, al, batch, w, steps, 3, flush)
+        cells = int(res["cells"].sum())
+        step_ms = sum(tot_ms) / len(tot_ms)
+        dtw_avg = sum(dtw_ms) / len(dtw_ms)
+        launches = al.stats(batch).launches
+        al.release(batch)
+        e2e = time_e2e(B, torch, al, w, 3, 1) if not args.no_e2e else None
+    finally:
+        al.close()
+        del al
+        torch.cuda.empty_cache()
+    dtw_gcups = cells / (dtw_avg / 1e3) / 1e9
+    out = {"workload": workload_name(args, name), "alignments": w.n_cands, "reads": w.n_reads,
+           "cells_per_step": cells, "value": round(cells / (step_ms / 1e3) / 1e9, 2), "unit": "GCUPS",
+           "ms_per_step": round(step_ms, 3), "dtw_kernel_ms": round(dtw_avg, 3),
+           "dtw_gcups": round(dtw_gcups, 2), "frac": round(dtw_gcups / peak, 4),
+           "steps": steps, "warmup": 3, "gpu_launches_per_step": int(launches),
+           "reads_per_s": round(w.n_reads / (step_ms / 1e3), 1), "generate_s": round(gen_s, 1)}
+    if e2e:
+        out["e2e"] = e2e
+    return out
 
 
 def main():
@@ -213,6 +405,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--extra", default="readuntil,longread,anchored",
+                    help="other full-size workloads measured after the headline one (comma list, or none)")
     ap.add_argument("--serve-chunks", type=int, default=10000)
     ap.add_argument("--serve-realtime-s", type=float, default=6.0)
     args = ap.parse_args()
@@ -233,59 +427,21 @@ def main():
     from paper_2310_05037_gb300 import binding as B
 
     w = make_workload(S, args, rank)
-    m_total = int(np.sum(w.cands["ref_len_bases"].astype(np.int64) - w.k + 1))
-    need = B.rawalign_dtw_batch_bytes(len(w.events), w.n_reads, w.n_cands, m_total)
-    arena = 3 * need + len(w.ref2bit) + (256 << 20)  # the prepared batch and two submissions in flight
-    if w.anchor_offsets is not None:  # per-gap work items and results, pieces
-        arena += 3 * (len(w.anchors) + w.n_cands) * 512
-    m_c = w.cands["ref_len_bases"].astype(np.int64) - w.k + 1
-    w_c = np.where(w.cands["band_w"] < 0, m_c, w.cands["band_w"].astype(np.int64))
-    if w.n_cands and int(np.max(2 * w_c + 1)) > 2000:
-        # bands too wide for shared-memory rings take ring scratch from the
-        # arena beyond batch_bytes; room for full grids in each batch
-        arena += 3 * (2 << 30)
+    arena, m_total = arena_bytes(B, w)
     al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena, device="cuda:%d" % local,
                    early_termination=args.workload == "batched_et")
-    stream = al.stream
     anchored = w.anchor_offsets is not None
-    if anchored:
-        batch = al.prepare_anchored(w.events, w.read_offsets, w.cands, w.anchors, w.anchor_offsets)
-    else:
-        batch = al.prepare(w.events, w.read_offsets, w.cands)
+    batch = prepare(al, w)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:%d" % local)
 
-    def one_step():
-        t = al.run(batch)
-        return t
-
-    for _ in range(args.warmup):
-        t = one_step()
-        res = al.poll(t, w.n_cands)
+    barrier(world)
+    clk = ClockSampler(local)
+    res, tot_ms, dtw_ms = time_resident(torch, al, batch, w, args.steps, args.warmup, flush, clk)
+    barrier(world)
     cells_step = int(res["cells"].sum())
     pruned_step = int(np.sum(res["status"] == B.RA_RESULT_PRUNED))
     reads_step = w.n_reads
     launches_step = al.stats(batch).launches
-
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    dtw_ms = []
-    tot_ms = []
-    barrier(world)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-                ev0[i].record(stream)
-            t = one_step()
-            with torch.cuda.stream(stream):
-                ev1[i].record(stream)
-            al.poll(t, 0)
-            st = al.stats(batch)
-            dtw_ms.append(st.dtw_ms)
-            tot_ms.append(ev0[i].elapsed_time(ev1[i]))
-        torch.cuda.synchronize()
-    barrier(world)
     clocks = clk.summary()
     step_ms = sum(tot_ms) / len(tot_ms)
     total_s = max_over_ranks(sum(tot_ms) / 1e3, world)
@@ -293,20 +449,24 @@ def main():
     value = total_cells / total_s / 1e9
     dtw_avg_ms = sum(dtw_ms) / len(dtw_ms)
 
-    peaks = load_peaks()
-    props = torch.cuda.get_device_properties(local)
-    sms = props.multi_processor_count
-    f_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_gcups = sms * 128 * f_max * 1e6 / OPS_PER_CELL / 1e9
+    sms, f_max, peak = peak_gcups(torch, local)
     achieved = cells_step / (dtw_avg_ms / 1e3) / 1e9
+    pipe = pipe_bound_gcups(sms, f_max)
     roofline = {
-        "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak_gcups, 1), "unit": "GCUPS",
-        "frac": round(achieved / peak_gcups, 4), "traffic": None,
+        "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "GCUPS",
+        "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(args.workload) if args.reads == 20000 else None,
         "kernel": "dtw_stripe_kernel", "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / %d ops per cell "
         "(derived, MEASURED_PEAKS sm_max_mhz)" % (sms, f_max, OPS_PER_CELL),
+        "pipe_bound": {"gcups": round(pipe, 1), "frac": round(achieved / pipe, 4),
+                       "alu_slots_per_cell": ALU_SLOTS_PER_CELL,
+                       "basis": "%d SMs x 64 ALU lanes per clock x %.0f MHz / ALU lane-slots per cell of the "
+                                "kernel's instruction mix (3-input min at half rate)" % (sms, f_max)},
     }
+    if roofline["traffic"] is not None:
+        roofline["traffic_per_cell_bytes"] = round(roofline["traffic"] / cells_step, 5)
+        roofline["traffic_basis"] = TRAFFIC_BASIS
     if clocks.get("sm_mhz"):
-        roofline["frac_at_measured_clock"] = round(achieved / (peak_gcups * clocks["sm_mhz"] / f_max), 4)
+        roofline["frac_at_measured_clock"] = round(achieved / (peak * clocks["sm_mhz"] / f_max), 4)
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
@@ -354,42 +514,11 @@ def main():
 
     # end to end through submit/poll with pinned host buffers
     if not args.no_e2e:
-        ev_h = torch.from_numpy(w.events).pin_memory()
-        off_h = torch.from_numpy(w.read_offsets.view(np.int64)).pin_memory()
-        cand_h = torch.from_numpy(w.cands.view(np.uint8)).pin_memory()
-        ev_np = ev_h.numpy()
-        off_np = off_h.numpy().view(np.uint64)
-        cand_np = cand_h.numpy().view(S.CANDIDATE_DTYPE)
-        def submit():
-            if anchored:
-                return B.rawalign_dtw_submit_anchored(al.h, ev_np, off_np, cand_np, w.anchors, w.anchor_offsets)
-            return B.rawalign_dtw_submit_batch(al.h, ev_np, off_np, cand_np)
-
-        def pipelined(steps):
-            # two submissions in flight: step i+1 is planned and uploaded while
-            # step i runs; every step copies its inputs in and its results out
-            t = submit()
-            r = None
-            for i in range(steps):
-                t_next = submit() if i + 1 < steps else None
-                r = B.rawalign_dtw_poll(al.h, t, w.n_cands)
-                t = t_next
-            return r
-
-        pipelined(2)
-        barrier(world)
-        t0 = time.perf_counter()
-        e2e_steps = max(3, args.steps // 2)
-        r = pipelined(e2e_steps)
-        el = max_over_ranks(time.perf_counter() - t0, world)
-        e2e_cells = sum_over_ranks(float(r["cells"].sum()) * e2e_steps, world)
-        out["e2e"] = {"value": round(e2e_cells / el / 1e9, 2), "unit": "GCUPS",
-                      "h2d_bytes_per_step": int(w.events.nbytes + w.read_offsets.nbytes + w.cands.nbytes +
-                                                (w.anchors.nbytes + w.anchor_offsets.nbytes
-                                                 if w.anchor_offsets is not None else 0)),
-                      "d2h_bytes_per_step": int(w.n_cands * B.RESULT_DTYPE.itemsize),
-                      "ms_per_step": round(el / e2e_steps * 1e3, 2),
-                      "pipelining": "two submissions in flight (submit i+1, then poll i)"}
+        out["e2e"] = time_e2e(B, torch, al, w, max(3, args.steps // 2), world)
+    al.release(batch)
+    al.close()
+    del al
+    torch.cuda.empty_cache()
 
     # Read-Until serving: 512 reads in flight, 180-event chunks, <= 4000 events
     if not args.no_serve and rank == 0:
@@ -416,13 +545,19 @@ def main():
         out["speedup_served_vs_plain"] = (round(closed["gcups"] / out["plain_kernel"]["gcups"], 1)
                                           if "plain_kernel" in out else None)
 
+    # the other full-size batch workloads, each measured the same way
+    extra = [x for x in args.extra.split(",") if x and x != "none" and x != args.workload]
+    if extra and rank == 0:
+        out["workloads"] = {}
+        for name in extra:
+            out["workloads"][name] = measure_extra(B, S, torch, args, name, local, flush, peak)
+
     if not args.no_cpu and rank == 0 and world >= 1:
         cb = cpu_baseline(w, seconds=args.cpu_seconds)
         cb["cores"] = 1
+        cb.update(host_cpu())
         out["cpu_baseline"] = {k: v for k, v in cb.items() if k != "seconds"}
 
-    al.release(batch)
-    al.close()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -452,7 +587,7 @@ def run_reference(args, S):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(secs), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(args), "reads": w.n_reads, "alignments": w.n_cands},
-        "cpu_baseline": {"value": round(value, 5), "unit": "GCUPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {**host_cpu(), "value": round(value, 5), "unit": "GCUPS", "cores": 1, "kind": "oracle",
                          "sample": "each step: random alignments of the workload for %.1f s, single thread; "
                                    "last: %s" % (per_step, samples[-1])},
         "e2e": {"value": round(value, 5), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

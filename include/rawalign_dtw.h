@@ -221,9 +221,11 @@ int rawalign_dtw_batch_stats(rawalign_dtw_t *h, uint64_t batch, rawalign_dtw_sta
  * not written (one alignment, no per-read decision).
  * Memory: the working rows live in one fixed array inside the library,
  * 3 * (65536 + 2) floats plus 256 bytes (about 0.8 MB) on every GPU that
- * loads the library, held until the process exits.  n_events above 65536 is
- * rejected with RA_EINVAL.  No cudaMalloc, cudaFree or allocating library
- * routine is called.  The first call on a device looks up that array's
+ * loads the library, held until the process exits.  n_events above 65536, or
+ * m of 2^30 or more, is rejected with RA_EINVAL.  No cudaMalloc, cudaFree or
+ * allocating library routine is called, and nothing is copied from host
+ * memory: the work record travels as a kernel parameter, so the call does
+ * not wait for earlier work on the stream.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress) with the device current; make that
  * first call before any stream capture.  Every call uses the same array and
  * leaves its contents behind: calls whose work overlaps on the GPU (other

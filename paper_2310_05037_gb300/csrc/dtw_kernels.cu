@@ -104,14 +104,13 @@ __device__ __forceinline__ long long floor_div_ll(long long a, long long b)
     return q;
 }
 
-__global__ void __launch_bounds__(256) dtw_plain_kernel(const WorkDesc *__restrict__ wdp,
-                                                        const float *__restrict__ events,
-                                                        const float *__restrict__ r_all,
-                                                        float *diag, rawalign_result_t *results,
-                                                        unsigned long long *best_keys, float b_match,
-                                                        int end_free)
+// The body of the plain kernel: one CTA, one alignment, one anti-diagonal
+// per __syncthreads (three rotating diagonal buffers of n+2 floats in diag).
+static __device__ __forceinline__ void plain_body(const WorkDesc &wd, const float *__restrict__ events,
+                                                  const float *__restrict__ r_all, float *diag,
+                                                  rawalign_result_t *results, unsigned long long *best_keys,
+                                                  float b_match, int end_free)
 {
-    const WorkDesc wd = *wdp;
     const int n = wd.nrows, m = wd.m;
     const long long num = wd.num, den = wd.den, w = wd.w, nd = num + den;
     const float *e = events + wd.ev_off;
@@ -189,6 +188,27 @@ __global__ void __launch_bounds__(256) dtw_plain_kernel(const WorkDesc *__restri
         o->status = 0;
         atomicMax(best_keys + wd.read, best_key(sc, wd.cand));
     }
+}
+
+__global__ void __launch_bounds__(256) dtw_plain_kernel(const WorkDesc *__restrict__ wdp,
+                                                        const float *__restrict__ events,
+                                                        const float *__restrict__ r_all,
+                                                        float *diag, rawalign_result_t *results,
+                                                        unsigned long long *best_keys, float b_match,
+                                                        int end_free)
+{
+    plain_body(*wdp, events, r_all, diag, results, best_keys, b_match, end_free);
+}
+
+// The same kernel with its work record passed by value (as a kernel
+// parameter), for callers that keep no work record in device memory.
+__global__ void __launch_bounds__(256) dtw_plain_kernel_byval(const WorkDesc wd, const float *__restrict__ events,
+                                                              const float *__restrict__ r_all, float *diag,
+                                                              rawalign_result_t *results,
+                                                              unsigned long long *best_keys, float b_match,
+                                                              int end_free)
+{
+    plain_body(wd, events, r_all, diag, results, best_keys, b_match, end_free);
 }
 
 // ---------------------------------------------------------------------------
@@ -305,6 +325,14 @@ cudaError_t launch_plain(const WorkDesc *w, const float *events, const float *r_
                          int end_free, cudaStream_t s)
 {
     dtw_plain_kernel<<<1, 256, 0, s>>>(w, events, r_all, diag, results, best_keys, b_match, end_free);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_byval(const WorkDesc &w, const float *events, const float *r_all, float *diag,
+                               rawalign_result_t *results, unsigned long long *best_keys, float b_match,
+                               int end_free, cudaStream_t s)
+{
+    dtw_plain_kernel_byval<<<1, 256, 0, s>>>(w, events, r_all, diag, results, best_keys, b_match, end_free);
     return cudaGetLastError();
 }
 

@@ -100,6 +100,9 @@ void *pick_stripe_et(int G, int HR, bool smem_ring);  // stripe_kernel_et.cu
 cudaError_t launch_plain(const WorkDesc *w, const float *events, const float *r_all, float *diag,
                          rawalign_result_t *results, unsigned long long *best_keys, float b_match,
                          int end_free, cudaStream_t s);
+cudaError_t launch_plain_byval(const WorkDesc &w, const float *events, const float *r_all, float *diag,
+                               rawalign_result_t *results, unsigned long long *best_keys, float b_match,
+                               int end_free, cudaStream_t s);
 int host_band(int64_t n, int64_t m, int32_t band_w, int64_t num, int64_t den, int64_t *num_out,
               int64_t *den_out, int64_t *w_out, int32_t *w_report);
 cudaError_t launch_combine(const CombineDesc *d, int n, const PieceRef *plan, const rawalign_result_t *pieces,

@@ -9,8 +9,9 @@
 // library itself (a static __device__ array, so every GPU that loads the
 // library holds it until the process exits).
 //
-// The work is the plain one-CTA kernel of dtw_kernels.cu, launched unchanged
-// with its scratch (three anti-diagonal buffers, its work record and the
+// The work is the plain one-CTA kernel of dtw_kernels.cu (its variant that
+// takes the work record by value, as a kernel parameter, so nothing is copied
+// from host memory), with its scratch (three anti-diagonal buffers and the
 // per-read best key) placed in that array.
 #include <cstring>
 #include <mutex>
@@ -20,7 +21,7 @@
 namespace {
 
 constexpr uint32_t kMaxRows = 1u << 16;  // events (DP rows) per alignment at most
-constexpr size_t kDescOff = 0;           // WorkDesc
+constexpr uint32_t kMaxCols = 1u << 30;  // expected values per alignment: below this (as the batch path)
 constexpr size_t kKeyOff = 128;          // per-read best key (8 bytes)
 constexpr size_t kDiagOff = 256;         // 3 * (kMaxRows + 2) floats
 constexpr size_t kScratchBytes = kDiagOff + sizeof(float) * 3 * ((size_t)kMaxRows + 2);
@@ -62,6 +63,8 @@ extern "C" int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_even
         return RA_EINVAL;
     if (n_events > kMaxRows)
         return RA_EINVAL;  // more rows than the fixed scratch holds
+    if (m >= kMaxCols)
+        return RA_EINVAL;  // the kernel's diagonal index n + m - 2 must stay a small int
     if (end_mode != RA_END_GLOBAL && end_mode != RA_END_FREE)
         return RA_EINVAL;
     ra::WorkDesc wd;
@@ -91,13 +94,11 @@ extern "C" int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_even
         return rc;
     char *b = (char *)base;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // the work record and the best key start fresh on every call; the
-    // diagonal buffers are reset by the kernel itself
-    if (cudaMemcpyAsync(b + kDescOff, &wd, sizeof wd, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(b + kKeyOff, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    // the best key starts fresh on every call (a device-side memset on the
+    // stream); the diagonal buffers are reset by the kernel itself
+    if (cudaMemsetAsync(b + kKeyOff, 0, sizeof(unsigned long long), s) != cudaSuccess)
         return RA_EDEVICE;
-    cudaError_t e = ra::launch_plain((const ra::WorkDesc *)(b + kDescOff), d_events, d_ref_signal,
-                                     (float *)(b + kDiagOff), d_result, (unsigned long long *)(b + kKeyOff), b_match,
-                                     end_mode == RA_END_FREE, s);
+    cudaError_t e = ra::launch_plain_byval(wd, d_events, d_ref_signal, (float *)(b + kDiagOff), d_result,
+                                           (unsigned long long *)(b + kKeyOff), b_match, end_mode == RA_END_FREE, s);
     return e == cudaSuccess ? RA_OK : RA_EDEVICE;
 }

@@ -5,13 +5,13 @@ classes, replays of the captured CUDA graphs), checked three ways:
   * every result against properties that hold at any size: status, record
     identity, GLOBAL end cell (n-1, m-1), score = fl(fl(B_Match * N_Read) - C)
     (Sec. 2.3), per-read best candidate and decision, identical replays;
-  * whole reads sampled at random (plus the extreme ones) against the FP32
-    oracle, bit for bit on every field, and against its FP64 run within
-    1e-5 relative;
-  * the longest alignments, too large for the oracle, between two bounds
-    that any warping path fixes: the sum over rows of the smallest in-band
-    |e_i - r_j| (every row holds at least one path cell, Sec. 2.2) and the
-    cost of one explicit in-band path along the band's centre line.
+  * every alignment of the plain, batched-uneven and Read-Until workloads
+    against the FP32 oracle, bit for bit on every field (the unchanged
+    single-threaded oracle, run on groups of whole reads over all host cores);
+    the long-read workload's eight longest alignments and forty random ones
+    the same way; sampled reads against the FP64 run within 1e-5 relative;
+  * the serving workload: 32 reads carried to 4000 events in 180-event chunks,
+    every chunk of every candidate against the oracle's DTW of the prefix.
 """
 import numpy as np
 import pytest
@@ -23,6 +23,7 @@ from paper_2310_05037_gb300 import binding as B  # noqa: E402
 from paper_2310_05037_gb300 import synth as S  # noqa: E402
 
 from gpu_util import run_gpu  # noqa: E402
+from oracle_pool import map_parallel  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -93,47 +94,6 @@ def _check_sample(w, g, idx):
     assert rel.max() < 1e-5, rel.max()
 
 
-def _expected(w, c):
-    cand = w.cands[c]
-    codes = O.segment_codes(w.ref2bit, w.ref_len, int(cand["ref_offset"]), int(cand["ref_len_bases"]),
-                            int(cand["strand"]))
-    return O.expected_signal(codes, w.k, w.pore).astype(np.float64)
-
-
-def _bounds(w, c):
-    """(lower, upper) bounds on the exact DTW cost of candidate c."""
-    cand = w.cands[c]
-    r0 = int(w.read_offsets[int(cand["read_id"])])
-    r1 = int(w.read_offsets[int(cand["read_id"]) + 1])
-    e = w.events[r0:r1].astype(np.float64)
-    r = _expected(w, c)
-    n, m = len(e), len(r)
-    band = O.band_params(n, m, int(cand["band_w"]), int(cand["slope_num"]), int(cand["slope_den"]))
-    assert not band.unbanded
-    num, den, wb = int(band.num), int(band.den), int(band.w_eff)
-    # lower: each row's smallest in-band difference (in-band columns of row i
-    # are the integers j with |j*den - i*num| <= w*den; checked at the ends)
-    lower = 0.0
-    for i in range(n):
-        lo = max(0, -((wb * den - i * num) // den))
-        hi = min(m - 1, (i * num + wb * den) // den)
-        assert O.in_band(band, i, lo) and O.in_band(band, i, hi)
-        assert not (lo > 0 and O.in_band(band, i, lo - 1)) and not (hi < m - 1 and O.in_band(band, i, hi + 1))
-        lower += float(np.min(np.abs(e[i] - r[lo:hi + 1])))
-    # upper: the staircase through c_i = floor(i*num/den); along row i it walks
-    # c_i .. c_{i+1}-1 and then steps diagonally (or down) to (i+1, c_{i+1})
-    ci = (np.arange(n, dtype=np.int64) * num) // den
-    upper = 0.0
-    for i in range(n):
-        j_end = ci[i + 1] - 1 if i + 1 < n else m - 1
-        j_end = max(j_end, ci[i])
-        js = np.arange(ci[i], j_end + 1)
-        for j in (int(js[0]), int(js[-1])):
-            assert O.in_band(band, i, j)
-        upper += float(np.sum(np.abs(e[i] - r[js])))
-    return lower, upper, n + m
-
-
 def _run_full(name):
     w = S.scaled(name, "full")
     outs = run_gpu(w, graph_runs=2)
@@ -144,6 +104,19 @@ def _run_full(name):
     return w, a
 
 
+def _check_all(w, g, idx=None, label=""):
+    """Every selected alignment against the FP32 oracle, bit for bit."""
+    o, info = map_parallel(w, idx)
+    gs = g if idx is None else g[idx]
+    bad = np.nonzero(gs["cost"].view(np.uint32) != o["cost"].astype(np.float32).view(np.uint32))[0]
+    assert len(bad) == 0, "cost differs at %s" % (bad[:8] if idx is None else np.asarray(idx)[bad[:8]])
+    assert np.array_equal(gs["score"].view(np.uint32), o["score"].astype(np.float32).view(np.uint32))
+    for f in ("read_id", "cand_idx", "end_i", "end_j", "w_eff", "cells", "is_best", "decision"):
+        assert np.array_equal(gs[f].astype(np.int64), o[f].astype(np.int64)), f
+    print("%s: %d alignments bit-exact vs the FP32 oracle (%.3g cells) in %.1f s on %d host threads"
+          % (label, len(o), float(o["cells"].sum()), info["seconds"], info["threads"]))
+
+
 def test_full_plain():
     w, g = _run_full("plain")
     _check_sample(w, g, np.arange(w.n_cands))
@@ -151,6 +124,7 @@ def test_full_plain():
 
 def test_full_batched():
     w, g = _run_full("batched")
+    _check_all(w, g, label="batched uneven")
     rng = np.random.default_rng(21)
     lens = w.read_lengths()
     counts = np.bincount(w.cands["read_id"].astype(np.int64), minlength=w.n_reads)
@@ -161,6 +135,7 @@ def test_full_batched():
 
 def test_full_readuntil():
     w, g = _run_full("readuntil")
+    _check_all(w, g, label="Read-Until prefix")
     rng = np.random.default_rng(22)
     counts = np.bincount(w.cands["read_id"].astype(np.int64), minlength=w.n_reads)
     reads = set(rng.choice(w.n_reads, 24, replace=False).tolist()) | {int(np.argmax(counts))}
@@ -169,16 +144,75 @@ def test_full_readuntil():
 
 def test_full_longread():
     w, g = _run_full("longread")
-    lens = w.read_lengths()
-    order = np.argsort(lens, kind="stable")
-    _check_sample(w, g, _whole_reads(w, order[:2]))
-    # the longest alignments: between the row-minimum and the centre-path bounds
     n, m = _dims(w)
-    for c in np.argsort(n * m, kind="stable")[-2:]:
-        lower, upper, steps = _bounds(w, int(c))
-        cost = float(g["cost"][c])
-        tol = steps * U32
-        assert lower * (1 - tol) <= cost <= upper * (1 + tol), (c, lower, cost, upper)
+    rng = np.random.default_rng(24)
+    longest = np.argsort(n * m, kind="stable")[-8:]
+    others = np.setdiff1d(np.arange(w.n_cands), longest)
+    idx = np.concatenate([longest, rng.choice(others, 40, replace=False)])
+    # whole reads, so that is_best and the decision are the oracle's too
+    idx = _whole_reads(w, np.unique(w.cands["read_id"][idx].astype(np.int64)))
+    _check_all(w, g, idx, label="long read (longest and random)")
+    # FP64: the rigorous bound (every DP value is a sum of at most n+m-1
+    # non-negative terms) and the measured relative difference
+    o64, _ = map_parallel(w, longest, use_f64=True)
+    rel = np.abs(g["cost"][longest].astype(np.float64) - o64["cost64"]) / o64["cost64"]
+    assert np.all(rel <= (n[longest] + m[longest]) * U32), rel
+    print("long read: FP32 vs FP64 relative difference of the 8 longest costs: max %.3g" % rel.max())
+
+
+def test_full_serving_to_max_events():
+    """Serving at the serving workload's sizes: 32 reads of up to 32
+    candidates carried to 4000 events in 180-event chunks (Sec. 3.1); every
+    chunk's result for every candidate equals the oracle's DTW of the prefix
+    aligned so far (FREE end, the candidate's slope), bit for bit."""
+    import concurrent.futures as cf
+
+    from oracle_pool import cores
+
+    pore, ref, ref_len, reads = S.config_serving(n_reads=32)
+    reads = [rd for rd in reads]
+    al = B.Aligner(pore, ref, ref_len, arena_bytes=len(ref) + (512 << 20), serve_slots=32,
+                   serve_max_events=4000, max_candidates=32)
+    got = {rd.read_id: [] for rd in reads}
+    try:
+        for p in range(0, 4000, 180):
+            q = min(p + 180, 4000)
+            tickets = [(rd, B.rawalign_dtw_submit_chunk(al.h, rd.read_id, rd.events[p:q],
+                                                        rd.cands if p == 0 else None, q == 4000))
+                       for rd in reads]
+            B.rawalign_dtw_flush(al.h)
+            for rd, t in tickets:
+                got[rd.read_id].append((q, B.rawalign_dtw_poll(al.h, t, 64)))
+    finally:
+        al.close()
+    O.lib()
+
+    def check(job):
+        rd, c = job
+        cand = rd.cands[c]
+        codes = O.segment_codes(ref, ref_len, int(cand["ref_offset"]), int(cand["ref_len_bases"]),
+                                int(cand["strand"]))
+        r = O.expected_signal(codes, 6, pore)
+        bad = []
+        for q, res in got[rd.read_id]:
+            cost, ei, ej, cells, weff = O.dtw_f32(rd.events[:q], r, int(cand["band_w"]), int(cand["slope_num"]),
+                                                  int(cand["slope_den"]), O.END_FREE)
+            sc = O.score_f32(0.4, q, cost)
+            gr = res[c]
+            if (np.float32(gr["cost"]).view(np.uint32) != np.float32(cost).view(np.uint32)
+                    or np.float32(gr["score"]).view(np.uint32) != np.float32(sc).view(np.uint32)
+                    or (int(gr["end_i"]), int(gr["end_j"])) != (ei, ej) or int(gr["cand_idx"]) != c
+                    or int(gr["read_id"]) != rd.read_id):
+                bad.append((rd.read_id, c, q))
+        return bad, len(got[rd.read_id])
+
+    jobs = [(rd, c) for rd in reads for c in range(len(rd.cands))]
+    with cf.ThreadPoolExecutor(max_workers=cores()) as ex:
+        outs = list(ex.map(check, jobs))
+    bad = [b for o, _ in outs for b in o]
+    assert not bad, bad[:8]
+    assert all(len(got[rd.read_id]) == 23 for rd in reads)
+    print("serving: %d candidate chunks bit-exact vs the oracle's prefix DTW" % sum(k for _, k in outs))
 
 
 def test_full_anchored():
