@@ -407,7 +407,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--extra", default="readuntil,longread,anchored",
                     help="other full-size workloads measured after the headline one (comma list, or none)")
-    ap.add_argument("--serve-chunks", type=int, default=10000)
+    ap.add_argument("--serve-chunks", type=int, default=30000)
     ap.add_argument("--serve-realtime-s", type=float, default=6.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -525,8 +525,9 @@ def main():
         from paper_2310_05037_gb300.serving import ServingLoop
 
         pore_s, ref_s, rl_s, sreads = S.config_serving(n_reads=4096)
-        als = B.Aligner(pore_s, ref_s, rl_s, arena_bytes=(len(ref_s) + (1536 << 20)), serve_slots=512,
-                        serve_max_events=4000, max_candidates=32, device="cuda:%d" % local)
+        als = B.Aligner(pore_s, ref_s, rl_s, arena_bytes=(len(ref_s) + (1536 << 20)), serve_slots=1024,
+                        serve_max_events=4000, max_candidates=32, device="cuda:%d" % local,
+                        serve_early_reject=True)
         loop = ServingLoop(als, sreads[:64])
         loop.run(max_chunks=300, in_flight=64)  # warm-up
         loop = ServingLoop(als, sreads)
@@ -541,7 +542,10 @@ def main():
         out["served"] = {"closed_loop": closed, "realtime": rt,
                          "decision_study": {"reads": len(trs), "by_threshold": study},
                          "workload": "Read-Until serving: Poisson stream, 512 reads in flight, 180-event chunks, "
-                                     "<= 4000 events, 1-32 candidates, band 64, FREE end, 50% off-target reads"}
+                                     "<= 4000 events, 1-32 candidates, band 64, FREE end, 50% off-target reads",
+                         "loop": "closed loop: two generations of 256 reads, one submit_chunks + flush + "
+                                 "poll_chunks per generation; reads stop at the library's decision (MAPPED, or "
+                                 "UNMAPPED once no candidate can reach the threshold within 4000 events)"}
         out["speedup_served_vs_plain"] = (round(closed["gcups"] / out["plain_kernel"]["gcups"], 1)
                                           if "plain_kernel" in out else None)
 

@@ -84,7 +84,8 @@ typedef struct {
     int32_t serve_max_events;  /* serving: events per read at most */
     const char *autotune_path; /* optional tuning table written by the tuner */
     int32_t early_termination; /* 1: branch and bound in GLOBAL batches (Sec. 2.4.1), see prepare_batch */
-    int32_t pad;
+    int32_t serve_early_reject;/* serving: 1 = decide RA_UNMAPPED as soon as no candidate can reach the
+                                  threshold within serve_max_events events (see submit_chunk) */
 } rawalign_dtw_config_t;
 
 /* One candidate region of the reference for one read (48 bytes). */
@@ -154,7 +155,13 @@ int rawalign_dtw_submit_batch(rawalign_dtw_t *h, const float *events, const uint
  * when no read slot or frontier memory is free (admission), RA_EINVAL for
  * unknown reads or bad data.  The chunk's results (one per candidate, with the
  * read's decision so far: RA_MAPPED, or RA_PENDING / RA_UNMAPPED when last)
- * come from rawalign_dtw_poll(ticket). */
+ * come from rawalign_dtw_poll(ticket).  With config.serve_early_reject = 1 a
+ * chunk that is not the last one is also decided RA_UNMAPPED when no
+ * candidate can reach the threshold any more: for every candidate
+ * fl(fl(B_Match * serve_max_events) - cost) < Score_Threshold.  Costs only
+ * grow as rows are added (every term is non-negative and rounding is
+ * monotone), so such a read can never be mapped; the caller stops it (an
+ * empty chunk with last = 1 returns its slot and memory). */
 int rawalign_dtw_submit_chunk(rawalign_dtw_t *h, uint64_t read_id, const float *events,
                               uint32_t n_events, const rawalign_candidate_t *cands,
                               uint32_t n_cands, int last, uint64_t *ticket);
@@ -163,6 +170,56 @@ int rawalign_dtw_submit_chunk(rawalign_dtw_t *h, uint64_t read_id, const float *
  * (serving); submit_chunk queues, flush runs.  Returns RA_OK when nothing is
  * pending. */
 int rawalign_dtw_flush(rawalign_dtw_t *h);
+
+/* One chunk of a batched serving submission (32 bytes): events
+ * events[ev_offset .. ev_offset+n_events) of read read_id; on the read's first
+ * chunk its candidates cands[cand_offset .. cand_offset+n_cands), later
+ * chunks n_cands = 0; last = 1 closes the read after this chunk (an empty
+ * chunk with last = 1 closes a read that the caller stops early). */
+typedef struct {
+    uint64_t read_id;
+    uint64_t ev_offset;
+    uint32_t n_events;
+    uint32_t cand_offset;
+    uint32_t n_cands;
+    int32_t last;
+} rawalign_chunk_t;
+
+/* Serving, many reads per call (Sec. 3.1: every pore delivers its next chunk
+ * at about the same time): the same as rawalign_dtw_submit_chunk for each of
+ * chunks[0 .. n_chunks) in order, from one events array and one candidates
+ * array (host memory, read before return).  tickets[i] and status[i] receive
+ * each chunk's ticket (0 when refused) and status (RA_OK, RA_EAGAIN when the
+ * read was not admitted: no read slot or arena memory free, RA_EINVAL for bad
+ * data); a refused chunk changes nothing.  Returns RA_OK, or RA_EINVAL for
+ * bad arguments (then nothing was queued). */
+int rawalign_dtw_submit_chunks(rawalign_dtw_t *h, const rawalign_chunk_t *chunks, uint32_t n_chunks,
+                               const float *events, const rawalign_candidate_t *cands, uint64_t *tickets,
+                               int32_t *status);
+
+/* Serving: waits up to timeout_us (0 = do not wait, < 0 = forever) until every
+ * ticket of tickets[0 .. n_tickets) has completed, then writes their results
+ * back to back, in ticket order, into out (host, cap entries) and each
+ * ticket's result count into counts[i].  Returns RA_ENOTREADY when some ticket
+ * is still running (nothing is consumed), RA_EINVAL for an unknown or repeated
+ * ticket or when cap is too small (nothing is consumed), RA_EDEVICE.  Each
+ * ticket is consumed once, as with rawalign_dtw_poll. */
+int rawalign_dtw_poll_chunks(rawalign_dtw_t *h, const uint64_t *tickets, uint32_t n_tickets,
+                             rawalign_result_t *out, uint32_t cap, uint32_t *counts, int64_t timeout_us);
+
+/* Serving counters since the handle was created (or the last reset): flushes,
+ * chunks and per-candidate pieces launched, in-band cells, host time spent
+ * queueing and planning (submit and flush calls), and per-flush device
+ * intervals measured with CUDA events: input copies, kernels, result copy. */
+typedef struct {
+    uint64_t flushes, chunks, pieces, cells;
+    double host_submit_ms;     /* in submit_chunk / submit_chunks */
+    double host_flush_ms;      /* in flush: planning, staging, launching */
+    double h2d_ms;             /* device time of the input copies */
+    double device_ms;          /* device time from the first kernel to the last */
+    double d2h_ms;             /* device time of the result copy */
+} rawalign_dtw_serve_stats_t;
+int rawalign_dtw_serve_stats(rawalign_dtw_t *h, rawalign_dtw_serve_stats_t *out, int reset);
 
 /* Waits up to timeout_us microseconds (0 = do not wait, < 0 = wait forever)
  * for a ticket, then copies up to cap results into out (host) and sets n_out.

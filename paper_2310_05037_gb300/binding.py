@@ -51,7 +51,7 @@ class Config(C.Structure):
         ("serve_max_events", C.c_int32),
         ("autotune_path", C.c_char_p),
         ("early_termination", C.c_int32),
-        ("pad", C.c_int32),
+        ("serve_early_reject", C.c_int32),
     ]
 
 
@@ -97,6 +97,29 @@ class Stats(C.Structure):
     ]
 
 
+class ServeStats(C.Structure):
+    _fields_ = [
+        ("flushes", C.c_uint64),
+        ("chunks", C.c_uint64),
+        ("pieces", C.c_uint64),
+        ("cells", C.c_uint64),
+        ("host_submit_ms", C.c_double),
+        ("host_flush_ms", C.c_double),
+        ("h2d_ms", C.c_double),
+        ("device_ms", C.c_double),
+        ("d2h_ms", C.c_double),
+    ]
+
+
+CHUNK_DTYPE = np.dtype(
+    {
+        "names": ["read_id", "ev_offset", "n_events", "cand_offset", "n_cands", "last"],
+        "formats": ["<u8", "<u8", "<u4", "<u4", "<u4", "<i4"],
+        "offsets": [0, 8, 16, 20, 24, 28],
+        "itemsize": 32,
+    }
+)
+
 RESULT_DTYPE = np.dtype(
     {
         "names": [f[0] for f in Result._fields_],
@@ -113,6 +136,11 @@ SIGNATURES = {
     "rawalign_dtw_submit_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, _u64p]),
     "rawalign_dtw_submit_chunk": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_int, _u64p]),
     "rawalign_dtw_flush": (C.c_int, [C.c_void_p]),
+    "rawalign_dtw_submit_chunks": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]),
+    "rawalign_dtw_poll_chunks": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_void_p,
+                                           C.c_int64]),
+    "rawalign_dtw_serve_stats": (C.c_int, [C.c_void_p, C.POINTER(ServeStats), C.c_int]),
     "rawalign_dtw_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.c_int64]),
     "rawalign_dtw_prepare_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, _u64p]),
     "rawalign_dtw_prepare_anchored": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
@@ -268,6 +296,42 @@ def rawalign_dtw_flush(h) -> None:
     _check("rawalign_dtw_flush", load().rawalign_dtw_flush(h))
 
 
+def rawalign_dtw_submit_chunks(h, chunks, events, cands):
+    """chunks: CHUNK_DTYPE array; events / cands: the arrays the chunks index.
+    Returns (tickets uint64 array, status int32 array)."""
+    ch = np.ascontiguousarray(chunks)
+    if ch.dtype != CHUNK_DTYPE:
+        raise TypeError("chunks must use CHUNK_DTYPE")
+    ev = np.ascontiguousarray(events, np.float32)
+    cd = np.ascontiguousarray(cands)
+    if cd.dtype != CANDIDATE_DTYPE:
+        raise TypeError("candidates must use CANDIDATE_DTYPE")
+    tickets = np.zeros(len(ch), np.uint64)
+    status = np.zeros(len(ch), np.int32)
+    _check("rawalign_dtw_submit_chunks", load().rawalign_dtw_submit_chunks(
+        h, _ptr(ch), len(ch), _ptr(ev), _ptr(cd), _ptr(tickets), _ptr(status)))
+    return tickets, status
+
+
+def rawalign_dtw_poll_chunks(h, tickets, cap: int, timeout_us: int = -1):
+    """Results of every ticket, back to back, and the count per ticket; None
+    while RA_ENOTREADY."""
+    t = np.ascontiguousarray(tickets, np.uint64)
+    out = np.zeros(max(int(cap), 1), RESULT_DTYPE)
+    counts = np.zeros(len(t), np.uint32)
+    code = load().rawalign_dtw_poll_chunks(h, _ptr(t), len(t), _ptr(out), int(cap), _ptr(counts), int(timeout_us))
+    if code == RA_ENOTREADY:
+        return None
+    _check("rawalign_dtw_poll_chunks", code)
+    return out[: int(counts.sum())], counts
+
+
+def rawalign_dtw_serve_stats(h, reset: bool = False) -> ServeStats:
+    s = ServeStats()
+    _check("rawalign_dtw_serve_stats", load().rawalign_dtw_serve_stats(h, C.byref(s), 1 if reset else 0))
+    return s
+
+
 def rawalign_dtw_poll(h, ticket: int, cap: int, timeout_us: int = -1):
     """Returns a structured array of results, or None while RA_ENOTREADY."""
     out = np.zeros(max(cap, 1), RESULT_DTYPE)
@@ -318,7 +382,7 @@ class Aligner:
     def __init__(self, pore, ref2bit, ref_len, arena_bytes=1 << 30, k=6, b_match=0.4, score_threshold=20.0,
                  end_mode=RA_END_GLOBAL, kernel=RA_KERNEL_AUTO, stream=None, serve_slots=0,
                  serve_max_events=0, max_candidates=64, device="cuda:0", autotune_path=None,
-                 early_termination=False):
+                 early_termination=False, serve_early_reject=False):
         import torch
 
         self.torch = torch
@@ -339,6 +403,7 @@ class Aligner:
         cfg.serve_slots = serve_slots
         cfg.serve_max_events = serve_max_events
         cfg.early_termination = 1 if early_termination else 0
+        cfg.serve_early_reject = 1 if serve_early_reject else 0
         self._tune_path = autotune_path.encode() if autotune_path else None
         cfg.autotune_path = self._tune_path
         self.cfg = cfg

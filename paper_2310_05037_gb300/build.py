@@ -3,7 +3,8 @@
 Each .cu under csrc/ compiles to an object in parallel; the objects link into
 paper_2310_05037_gb300/librawalign_dtw.so.  No fast-math: IEEE FP32 with
 round-to-nearest, no flush-to-zero, and -fmad=false so no multiply-add can be
-contracted anywhere in device code.
+contracted anywhere in device code (-ffp-contract=off does the same for the
+host compiler).
 """
 from __future__ import annotations
 
@@ -22,7 +23,7 @@ BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-fno-fast-math", "-I", INCLUDE, "-I", CSRC]
+           "-Xcompiler", "-fno-fast-math", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:

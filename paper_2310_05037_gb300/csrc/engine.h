@@ -581,12 +581,24 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
             ord[x] = (int)x;
         }
     });
+    if (n <= 16384) {
+        // small batches (serving flushes): a comparison sort of (key, index)
+        // pairs gives the same order without the radix passes' 64 K counters
+        std::vector<std::pair<uint64_t, int>> kv(n);
+        for (size_t x = 0; x < n; ++x)
+            kv[x] = {key[x], (int)x};
+        std::sort(kv.begin(), kv.end());
+        for (size_t x = 0; x < n; ++x) {
+            key[x] = kv[x].first;
+            ord[x] = kv[x].second;
+        }
+    }
     // each pass: per-chunk digit counts, offsets in (digit, chunk) order,
     // then every chunk scatters its items in order (stable)
     const size_t T = std::max<size_t>(1, std::min<size_t>(host_threads(), n / (1 << 16)));
-    std::vector<uint32_t> cnt(T << 16), tot(1 << 16);
+    std::vector<uint32_t> cnt(n > 16384 ? (T << 16) : 0), tot(n > 16384 ? (1 << 16) : 0);
     auto chunks = [&](auto fn) { run_tasks((unsigned)T, [&](unsigned t) { fn((size_t)t); }); };
-    for (int shift = 0; shift < 48 && n > 1; shift += 16) {
+    for (int shift = 0; shift < 48 && n > 16384; shift += 16) {
         chunks([&](size_t t) {
             uint32_t *c = cnt.data() + (t << 16);
             std::fill(c, c + (1 << 16), 0u);

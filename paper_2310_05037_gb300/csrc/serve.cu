@@ -15,6 +15,9 @@
 // the GPU go into the next flush, and the stream orders the flushes, so a
 // read's chunk k+1 always sees the frontier chunk k wrote.  A read's memory
 // and slot are returned when the flush carrying its last chunk completes.
+#include <unordered_map>
+#include <unordered_set>
+
 #include "engine.h"
 
 namespace ra_host {
@@ -30,6 +33,8 @@ struct ServeCand {
     uint32_t m = 0;
     bool dead = false;      // the band has left the table: no cell any more
     SigDesc sig{};
+    int64_t plan_rows = -1; // chunk height of the cached variant choice
+    int plan_variant = 0;   // variant chosen for chunks of plan_rows rows
 };
 
 struct ServeRead {
@@ -84,6 +89,7 @@ struct PinnedPool {
 
 struct FlushRec {
     cudaEvent_t done = nullptr;
+    cudaEvent_t t_ev[3] = {nullptr, nullptr, nullptr};  // timing: start, inputs copied, kernels done
     std::vector<void *> blocks;
     rawalign_result_t *d_res = nullptr;
     rawalign_result_t *h_res = nullptr;  // pinned
@@ -95,6 +101,7 @@ struct FlushRec {
     };
     std::vector<T> tickets;
     std::vector<uint64_t> closing;  // reads whose memory is returned on completion
+    uint32_t n_items = 0;           // per-candidate results in h_res
     bool reaped = false;
 };
 
@@ -108,8 +115,11 @@ struct ServeState {
     std::map<uint64_t, FlushRec *> flushes;       // by flush id
     std::map<uint64_t, uint64_t> ticket_flush;    // ticket -> flush id
     std::map<uint64_t, std::vector<rawalign_result_t>> ready;  // reaped results by ticket
+    std::unordered_map<uint64_t, size_t> pending_at;           // read id -> index in pending
     uint64_t next_flush = 1;
     PinnedPool pinned;
+    std::vector<cudaEvent_t> timing_events;  // reusable timing events
+    rawalign_dtw_serve_stats_t stats{};
 };
 
 namespace {
@@ -138,21 +148,53 @@ void release_read(rawalign_dtw *h, ServeState *st, uint64_t read_id)
 }
 
 // Copies a completed flush's results to its tickets and returns its memory.
+// Early reject (config.serve_early_reject): true when no candidate of the
+// chunk can reach the threshold within max_events events.  Each candidate's
+// best possible score is fl(fl(B * max_events) - cost): the cost of a FREE end
+// never decreases as rows are added, and both roundings are monotone.
+bool unreachable(const rawalign_result_t *r, uint32_t n, float b_match, uint32_t max_events, float thr)
+{
+    volatile float xb = b_match * (float)max_events;  // rounded once, never contracted with the subtraction
+    for (uint32_t c = 0; c < n; ++c) {
+        volatile float best = xb - r[c].cost;
+        if (best >= thr)
+            return false;
+    }
+    return true;
+}
+
 void reap(rawalign_dtw *h, ServeState *st, uint64_t fid, FlushRec *f)
 {
     if (f->reaped)
         return;
+    const bool reject = h->cfg.serve_early_reject && st->max_events > 0;
     for (auto &t : f->tickets) {
         std::vector<rawalign_result_t> v(f->h_res + t.first, f->h_res + t.first + t.count);
+        const bool dead = reject && !t.last && t.count && v[0].decision == RA_PENDING &&
+                          unreachable(v.data(), t.count, h->cfg.b_match, st->max_events, h->cfg.score_threshold);
         for (uint32_t c = 0; c < t.count; ++c) {
             v[c].read_id = t.read_id;
             v[c].cand_idx = c;
-            if (t.last && v[c].decision == RA_PENDING)
+            if ((t.last || dead) && v[c].decision == RA_PENDING)
                 v[c].decision = RA_UNMAPPED;
         }
         st->ready[t.ticket] = std::move(v);
         st->ticket_flush.erase(t.ticket);
     }
+    if (f->t_ev[0]) {
+        float a = 0, b = 0, c = 0;
+        if (cudaEventElapsedTime(&a, f->t_ev[0], f->t_ev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, f->t_ev[1], f->t_ev[2]) == cudaSuccess &&
+            cudaEventElapsedTime(&c, f->t_ev[2], f->done) == cudaSuccess) {
+            st->stats.h2d_ms += a;
+            st->stats.device_ms += b;
+            st->stats.d2h_ms += c;
+        }
+        for (cudaEvent_t e : f->t_ev)
+            st->timing_events.push_back(e);
+    }
+    for (uint32_t x = 0; x < f->n_items; ++x)
+        st->stats.cells += f->h_res[x].cells;
     for (void *p : f->blocks)
         h->arena.release(p);
     f->blocks.clear();
@@ -160,7 +202,10 @@ void reap(rawalign_dtw *h, ServeState *st, uint64_t fid, FlushRec *f)
     st->pinned.put(f->h_in);
     for (uint64_t r : f->closing)
         release_read(h, st, r);
-    cudaEventDestroy(f->done);
+    if (f->t_ev[0])
+        st->timing_events.push_back(f->done);  // a timing event too
+    else
+        cudaEventDestroy(f->done);
     f->reaped = true;
     st->flushes.erase(fid);
     delete f;
@@ -194,6 +239,8 @@ void serve_destroy(rawalign_dtw *h)
         rs.push_back(kv.first);
     for (uint64_t r : rs)
         release_read(h, st, r);
+    for (cudaEvent_t e : st->timing_events)
+        cudaEventDestroy(e);
     delete st;
     h->serve = nullptr;
 }
@@ -252,16 +299,14 @@ int serve_poll(rawalign_dtw *h, uint64_t ticket, rawalign_result_t *out, uint32_
 
 }  // namespace ra_host
 
-extern "C" int rawalign_dtw_submit_chunk(rawalign_dtw_t *h, uint64_t read_id, const float *events, uint32_t n_events,
-                                         const rawalign_candidate_t *cands, uint32_t n_cands, int last,
-                                         uint64_t *ticket)
+namespace ra_host {
+namespace {
+
+// Queues one chunk (the body of rawalign_dtw_submit_chunk); nothing changes
+// when it returns an error.
+int submit_one(rawalign_dtw *h, ServeState *st, uint64_t read_id, const float *events, uint32_t n_events,
+               const rawalign_candidate_t *cands, uint32_t n_cands, int last, uint64_t *ticket)
 {
-    if (!h || !ticket || (n_events && !events))
-        return RA_EINVAL;
-    ServeState *st = state(h);
-    if (!st)
-        return RA_EINVAL;  // serving not configured (serve_slots == 0)
-    cudaSetDevice(h->device);
     for (uint32_t x = 0; x < n_events; ++x)
         if (!std::isfinite(events[x]))
             return RA_EINVAL;
@@ -323,13 +368,14 @@ extern "C" int rawalign_dtw_submit_chunk(rawalign_dtw_t *h, uint64_t read_id, co
         return RA_EINVAL;
     // one pending chunk per read per flush: later chunks join it
     PendingChunk *pc = nullptr;
-    for (auto &p : st->pending)
-        if (p.read_id == read_id)
-            pc = &p;
+    auto pa = st->pending_at.find(read_id);
+    if (pa != st->pending_at.end())
+        pc = &st->pending[pa->second];
     uint64_t queued = pc ? pc->ev.size() : 0;
     if (st->max_events && rd.rows_done + queued + n_events > st->max_events)
         return RA_EINVAL;
     if (!pc) {
+        st->pending_at[read_id] = st->pending.size();
         st->pending.push_back(PendingChunk());
         pc = &st->pending.back();
         pc->read_id = read_id;
@@ -344,6 +390,60 @@ extern "C" int rawalign_dtw_submit_chunk(rawalign_dtw_t *h, uint64_t read_id, co
     return RA_OK;
 }
 
+double ms_since(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+}  // namespace ra_host
+
+extern "C" int rawalign_dtw_submit_chunk(rawalign_dtw_t *h, uint64_t read_id, const float *events, uint32_t n_events,
+                                         const rawalign_candidate_t *cands, uint32_t n_cands, int last,
+                                         uint64_t *ticket)
+{
+    if (!h || !ticket || (n_events && !events))
+        return RA_EINVAL;
+    ServeState *st = state(h);
+    if (!st)
+        return RA_EINVAL;  // serving not configured (serve_slots == 0)
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaSetDevice(h->device);
+    const int rc = submit_one(h, st, read_id, events, n_events, cands, n_cands, last, ticket);
+    st->stats.host_submit_ms += ms_since(t0);
+    return rc;
+}
+
+extern "C" int rawalign_dtw_submit_chunks(rawalign_dtw_t *h, const rawalign_chunk_t *chunks, uint32_t n_chunks,
+                                          const float *events, const rawalign_candidate_t *cands, uint64_t *tickets,
+                                          int32_t *status)
+{
+    if (!h || (n_chunks && (!chunks || !tickets || !status)))
+        return RA_EINVAL;
+    ServeState *st = state(h);
+    if (!st)
+        return RA_EINVAL;
+    for (uint32_t c = 0; c < n_chunks; ++c)
+        if ((chunks[c].n_events && !events) || (chunks[c].n_cands && !cands))
+            return RA_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaSetDevice(h->device);
+    for (uint32_t c = 0; c < n_chunks; ++c) {
+        const rawalign_chunk_t &ch = chunks[c];
+        tickets[c] = 0;
+        status[c] = submit_one(h, st, ch.read_id, ch.n_events ? events + ch.ev_offset : nullptr, ch.n_events,
+                               ch.n_cands ? cands + ch.cand_offset : nullptr, ch.n_cands, ch.last, &tickets[c]);
+        if (status[c] != RA_OK)
+            tickets[c] = 0;
+    }
+    st->stats.host_submit_ms += ms_since(t0);
+    return RA_OK;
+}
+
+namespace {
+int flush_impl(rawalign_dtw *h, ServeState *st);
+}
+
 extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
 {
     if (!h)
@@ -351,7 +451,16 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
     ServeState *st = h->serve;
     if (!st)
         return RA_OK;
+    const auto t0 = std::chrono::steady_clock::now();
     cudaSetDevice(h->device);
+    const int rc = flush_impl(h, st);
+    st->stats.host_flush_ms += ms_since(t0);
+    return rc;
+}
+
+namespace {
+int flush_impl(rawalign_dtw *h, ServeState *st)
+{
     reap_done(h, st);
     if (st->pending.empty())
         return RA_OK;
@@ -410,8 +519,19 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
             if (sc.dead) {
                 it.variant = 0;
                 sch.s_end = 0;
+            } else if (sc.plan_rows == (int64_t)nrows) {
+                // chunks of one height get one variant: the choice hardly
+                // depends on where the rows start (the results never do)
+                it.variant = sc.plan_variant;
+                sch = schedule(sc.band, row0, nrows, kVariants[it.variant][0], kVariants[it.variant][1]);
+                if (sch.s_end <= 0)
+                    it.variant = 0;
             } else {
                 it.variant = choose_variant(sc.band, row0, nrows, sch, h->slot_cost);
+                if (sch.s_end > 0) {
+                    sc.plan_rows = nrows;
+                    sc.plan_variant = it.variant;
+                }
             }
             wd.dC = sch.dC;
             wd.a0 = sch.a0;
@@ -450,6 +570,7 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
         for (auto &t : f->tickets)
             st->ticket_flush[t.ticket] = fid;
         st->pending.clear();
+        st->pending_at.clear();
         return RA_OK;
     }
     std::vector<int> order;
@@ -503,7 +624,19 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
     memcpy(hin + o_work, work.data(), b_work);
     memcpy(hin + o_rd, read_of.data(), b_rd);
     cudaStream_t s = h->stream;
-    RA_CUDA(cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming));
+    // timing events (start, inputs copied, kernels done, done), reused
+    while (st->timing_events.size() < 4) {
+        cudaEvent_t e = nullptr;
+        RA_CUDA(cudaEventCreate(&e));
+        st->timing_events.push_back(e);
+    }
+    for (int q = 0; q < 3; ++q) {
+        f->t_ev[q] = st->timing_events.back();
+        st->timing_events.pop_back();
+    }
+    f->done = st->timing_events.back();
+    st->timing_events.pop_back();
+    RA_CUDA(cudaEventRecord(f->t_ev[0], s));
     RA_CUDA(cudaMemcpyAsync(d_ev, hin, b_ev, cudaMemcpyHostToDevice, s));
     if (!sig.empty())
         RA_CUDA(cudaMemcpyAsync(d_sig, hin + o_sig, b_sig, cudaMemcpyHostToDevice, s));
@@ -511,6 +644,7 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
     RA_CUDA(cudaMemcpyAsync(d_read_of, hin + o_rd, b_rd, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemsetAsync(d_keys, 0, sizeof(unsigned long long) * chunk_idx, s));
     RA_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int) * (kMaxClasses + 2), s));
+    RA_CUDA(cudaEventRecord(f->t_ev[1], s));
     float *abase = (float *)h->arena.base;
     if (!sig.empty())
         RA_CUDA(launch_expected_signal(d_sig, (int)sig.size(), h->d_ref, h->d_pore, h->cfg.k, abase, s));
@@ -540,6 +674,8 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
         RA_CUDA(cudaStreamWaitEvent(s, h->join[ci], 0));
     }
     RA_CUDA(launch_decide(f->d_res, (int)n_items, d_keys, d_read_of, h->cfg.score_threshold, 0, s));
+    RA_CUDA(cudaEventRecord(f->t_ev[2], s));
+    f->n_items = n_items;
     RA_CUDA(cudaMemcpyAsync(f->h_res, f->d_res, sizeof(rawalign_result_t) * n_items, cudaMemcpyDeviceToHost, s));
     RA_CUDA(cudaEventRecord(f->done, s));
     // launched: advance the host-side read state
@@ -555,10 +691,108 @@ extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
         rd.signal_done = true;
         rd.rows_done += (uint32_t)pc.ev.size();
     }
+    st->stats.flushes++;
+    st->stats.chunks += chunk_idx;
+    st->stats.pieces += n_items;
     const uint64_t fid = st->next_flush++;
     st->flushes[fid] = f;
     for (auto &t : f->tickets)
         st->ticket_flush[t.ticket] = fid;
     st->pending.clear();
+    st->pending_at.clear();
+    return RA_OK;
+}
+}  // namespace
+
+extern "C" int rawalign_dtw_poll_chunks(rawalign_dtw_t *h, const uint64_t *tickets, uint32_t n_tickets,
+                                        rawalign_result_t *out, uint32_t cap, uint32_t *counts, int64_t timeout_us)
+{
+    if (!h || (n_tickets && (!tickets || !counts)) || (cap && !out))
+        return RA_EINVAL;
+    ServeState *st = h->serve;
+    if (!st)
+        return RA_EINVAL;
+    cudaSetDevice(h->device);
+    // every ticket known and named once; the flushes still to wait for
+    std::unordered_set<uint64_t> seen;
+    std::vector<uint64_t> wait_for;
+    for (uint32_t x = 0; x < n_tickets; ++x) {
+        const uint64_t t = tickets[x];
+        if (!seen.insert(t).second)
+            return RA_EINVAL;
+        if (st->ready.count(t))
+            continue;
+        auto tf = st->ticket_flush.find(t);
+        if (tf != st->ticket_flush.end()) {
+            wait_for.push_back(tf->second);
+            continue;
+        }
+        for (auto &pc : st->pending)
+            for (uint64_t q : pc.tickets)
+                if (q == t)
+                    return RA_ENOTREADY;  // queued, not flushed: waiting would not help
+        return RA_EINVAL;
+    }
+    std::sort(wait_for.begin(), wait_for.end());
+    wait_for.erase(std::unique(wait_for.begin(), wait_for.end()), wait_for.end());
+    const auto t0 = std::chrono::steady_clock::now();
+    for (uint64_t fid : wait_for) {
+        FlushRec *f = st->flushes[fid];
+        while (true) {
+            cudaError_t e = cudaEventQuery(f->done);
+            if (e == cudaSuccess)
+                break;
+            if (e != cudaErrorNotReady)
+                return cuda_ok(e);
+            if (timeout_us == 0)
+                return RA_ENOTREADY;
+            if (timeout_us < 0) {
+                RA_CUDA(cudaEventSynchronize(f->done));
+                break;
+            }
+            if (ms_since(t0) * 1e3 >= (double)timeout_us)
+                return RA_ENOTREADY;
+            std::this_thread::yield();
+        }
+    }
+    for (uint64_t fid : wait_for) {
+        auto it = st->flushes.find(fid);
+        if (it != st->flushes.end())
+            reap(h, st, fid, it->second);
+    }
+    uint64_t total = 0;
+    for (uint32_t x = 0; x < n_tickets; ++x) {
+        auto r = st->ready.find(tickets[x]);
+        if (r == st->ready.end())
+            return RA_EDEVICE;
+        total += r->second.size();
+    }
+    if (total > cap)
+        return RA_EINVAL;
+    uint64_t pos = 0;
+    for (uint32_t x = 0; x < n_tickets; ++x) {
+        auto r = st->ready.find(tickets[x]);
+        const size_t n = r->second.size();
+        if (n)
+            memcpy(out + pos, r->second.data(), sizeof(rawalign_result_t) * n);
+        counts[x] = (uint32_t)n;
+        pos += n;
+        st->ready.erase(r);
+    }
+    return RA_OK;
+}
+
+extern "C" int rawalign_dtw_serve_stats(rawalign_dtw_t *h, rawalign_dtw_serve_stats_t *out, int reset)
+{
+    if (!h || !out)
+        return RA_EINVAL;
+    ServeState *st = h->serve;
+    if (!st) {
+        memset(out, 0, sizeof *out);
+        return RA_OK;
+    }
+    *out = st->stats;
+    if (reset)
+        memset(&st->stats, 0, sizeof st->stats);
     return RA_OK;
 }

@@ -2,9 +2,15 @@
 // is in stripe_kernel.cuh) and its launchers.  The early-terminating
 // instantiations live in stripe_kernel_et.cu so that the two sets compile in
 // parallel.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "stripe_kernel.cuh"
 
 namespace ra {
+
+int stripe_max_blocks_uncached(int G, int HR, int block, size_t smem);
 
 // ---------------------------------------------------------------------------
 // variant table and launchers
@@ -35,7 +41,30 @@ static void *pick_stripe(int G, int HR, bool freeend, bool smem_ring)
     return nullptr;
 }
 
+// Resident blocks per SM of a variant (occupancy query, cached per device
+// and shape: serving asks for it on every flush).
 int stripe_max_blocks_per_sm(int G, int HR, int block, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, G, HR, block, smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end())
+            return it->second;
+    }
+    const int nb = stripe_max_blocks_uncached(G, HR, block, smem);
+    if (nb > 0) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = nb;
+    }
+    return nb;
+}
+
+int stripe_max_blocks_uncached(int G, int HR, int block, size_t smem)
 {
     void *fn = pick_stripe(G, HR, false, smem > 0);
     void *fn2 = pick_stripe(G, HR, true, smem > 0);

@@ -1,12 +1,13 @@
-"""Read-Until request loop over the C ABI (submit_chunk / flush / poll).
+"""Read-Until request loop over the C ABI (submit_chunks / flush / poll_chunks).
 
 Reads deliver their signal in chunks of events; after every chunk the library
 reports, per candidate, the cost and score of the prefix aligned so far and
-the read's decision (Sec. 2.3).  The loop stops a read when it is mapped
-(accept), when no candidate can reach Score_Threshold any more even if every
-remaining event matched perfectly (reject: B_Match * max_events - cost <
-threshold, the cost can only grow), or at max_events.  Stopped reads are
-closed, which returns their slot and device memory to the library.
+the read's decision (Sec. 2.3): MAPPED (accept), UNMAPPED (reject: with the
+handle's serve_early_reject, as soon as no candidate can reach
+Score_Threshold any more even if every remaining event up to max_events
+matched exactly; the cost only grows), or PENDING.  The loop stops a read at
+its decision or at max_events; a read stopped early is closed with an empty
+last chunk, which returns its slot and device memory to the library.
 
 Two modes:
   closed loop: a fixed number of reads in flight; a read's next chunk is
@@ -15,11 +16,16 @@ Two modes:
   real time:   reads arrive as a Poisson stream and every chunk becomes
                available chunk_s seconds after the previous one (latency at the
                sequencer's pace).
-Every flush launches all chunks queued since the previous flush as one batch
-(continuous batching).  Chunk latency = time from submit to result visible.
+Every round submits the chunks of every ready read in one call and launches
+them as one flush (continuous batching).  In closed loop the reads are split
+into two generations: while one generation's flush runs on the GPU, the
+other's results are read back, decided and its next chunks submitted, so the
+host work of one generation overlaps the device work of the other.  Chunk
+latency = time from submit to result visible on the host.
 """
 from __future__ import annotations
 
+import collections
 import dataclasses
 import time
 
@@ -37,138 +43,198 @@ class ServeStats:
     rejected: int = 0
     exhausted: int = 0
     wall_s: float = 0.0
+    flushes: int = 0
     latencies_ms: list = dataclasses.field(default_factory=list)
+    host: dict = dataclasses.field(default_factory=dict)
 
     def summary(self):
-        lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
-        return {
+        lat = np.concatenate([np.asarray(x, np.float64).ravel() for x in self.latencies_ms]) \
+            if self.latencies_ms else np.zeros(1)
+        out = {
             "chunks": self.chunks, "reads_decided": self.reads_done, "accepted": self.accepted,
             "rejected": self.rejected, "max_events": self.exhausted, "wall_s": round(self.wall_s, 3),
             "gcups": round(self.cells / max(self.wall_s, 1e-9) / 1e9, 3),
             "reads_per_s": round(self.reads_done / max(self.wall_s, 1e-9), 1),
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "flushes": self.flushes,
         }
-
-
-class _Live:
-    __slots__ = ("rd", "pos", "ticket", "t_submit", "next_ready")
-
-    def __init__(self, rd, next_ready):
-        self.rd = rd
-        self.pos = 0
-        self.ticket = None
-        self.t_submit = 0.0
-        self.next_ready = next_ready
+        if self.host:
+            out["breakdown_ms"] = {k: round(v, 2) for k, v in self.host.items()}
+        return out
 
 
 class ServingLoop:
-    def __init__(self, aligner, reads, chunk=180, max_events=4000, b_match=0.4, threshold=20.0):
+    def __init__(self, aligner, reads, chunk=180, max_events=4000):
         self.al = aligner
         self.reads = list(reads)
         self.chunk = chunk
         self.max_events = max_events
-        self.b_match = b_match
-        self.threshold = threshold
+        n = len(self.reads)
+        # every read's events (up to max_events) and candidates back to back:
+        # chunks index into these arrays, nothing is copied per chunk
+        self.n_ev = np.array([min(len(rd.events), max_events) for rd in self.reads], np.int64)
+        self.ev_off = np.zeros(n + 1, np.int64)
+        self.ev_off[1:] = np.cumsum(self.n_ev)
+        self.events = (np.concatenate([rd.events[:max_events] for rd in self.reads]).astype(np.float32)
+                       if n else np.zeros(0, np.float32))
+        self.n_cand = np.array([len(rd.cands) for rd in self.reads], np.int64)
+        self.cand_off = np.zeros(n + 1, np.int64)
+        self.cand_off[1:] = np.cumsum(self.n_cand)
+        self.cands = np.concatenate([rd.cands for rd in self.reads]) if n else np.zeros(0, B.CANDIDATE_DTYPE)
+        self.read_id = np.array([rd.read_id for rd in self.reads], np.uint64)
 
-    def _decide(self, live, res, st):
-        """True when the read stops after this result."""
-        n = live.pos
-        if len(res) and np.any(res["decision"] == B.RA_MAPPED):
-            st.accepted += 1
-            return True
-        best_possible = self.b_match * self.max_events - res["cost"].astype(np.float64)
-        if len(res) == 0 or np.all(best_possible < self.threshold):
-            st.rejected += 1
-            return True
-        if n >= min(self.max_events, len(live.rd.events)):
-            st.exhausted += 1
-            return True
-        return False
-
-    def _submit(self, live, now):
-        rd = live.rd
-        p = live.pos
-        q = min(p + self.chunk, len(rd.events), self.max_events)
-        last = q >= min(self.max_events, len(rd.events))
-        live.ticket = B.rawalign_dtw_submit_chunk(self.al.h, rd.read_id, rd.events[p:q],
-                                                  rd.cands if p == 0 else None, last)
-        live.t_submit = now
-        live.pos = q
-        return last
+    def _chunks(self, q, pos, close):
+        """Chunk records for reads q (the next chunk from pos; close: empty
+        closing chunks)."""
+        ch = np.zeros(len(q), B.CHUNK_DTYPE)
+        ch["read_id"] = self.read_id[q]
+        if close:
+            ch["last"] = 1
+            return ch
+        end = self.n_ev[q]
+        stop = np.minimum(pos + self.chunk, end)
+        ch["ev_offset"] = self.ev_off[q] + pos
+        ch["n_events"] = stop - pos
+        first = pos == 0
+        ch["cand_offset"] = np.where(first, self.cand_off[q], 0)
+        ch["n_cands"] = np.where(first, self.n_cand[q], 0)
+        ch["last"] = (stop >= end).astype(np.int32)
+        return ch
 
     def run(self, max_chunks=10_000, in_flight=512, realtime=False, chunk_s=0.4, duration_s=None,
-            arrival_rate=None):
+            arrival_rate=None, generations=2):
+        """Closed loop (default) or real time; returns ServeStats."""
+        h = self.al.h
         st = ServeStats()
-        pending_reads = list(self.reads)
-        live = {}
-        closed = []
-        t0 = time.perf_counter()
+        n = len(self.reads)
+        pos = np.zeros(n, np.int64)            # events submitted so far
+        ready_at = np.zeros(n, np.float64)     # when the read's next chunk may go
+        live = np.zeros(n, bool)               # admitted and not decided
+        busy = np.zeros(n, bool)               # a chunk in flight
+        pending = collections.deque(range(n))  # reads not admitted yet
+        to_close = []                          # reads decided early, still open in the library
+        gens = collections.deque()             # (tickets, reads, t_submit, closing tickets)
         rng = np.random.default_rng(1)
+        t_sub = t_flush = t_poll = 0.0
+        B.rawalign_dtw_serve_stats(h, reset=True)
+        t0 = time.perf_counter()
         next_arrival = t0
+        gen_cap = in_flight if realtime else max(1, -(-in_flight // max(1, generations)))
+
         while True:
             now = time.perf_counter()
             if duration_s is not None and now - t0 > duration_s:
                 break
-            if st.chunks >= max_chunks or (not pending_reads and not live):
+            if st.chunks >= max_chunks:
                 break
-            # admit new reads (closed loop: keep in_flight busy; real time: Poisson arrivals)
-            while pending_reads and len(live) < in_flight and (not realtime or now >= next_arrival):
-                rd = pending_reads.pop(0)
-                lv = _Live(rd, now)
-                try:
-                    self._submit(lv, now)
-                except B.RawAlignError as e:
-                    if e.code == B.RA_EAGAIN:  # admission refused: retry later
-                        pending_reads.insert(0, rd)
-                        break
-                    raise
-                live[rd.read_id] = lv
+            if not pending and not live.any() and not gens and not to_close:
+                break
+            # admission: closed loop keeps in_flight reads live, real time
+            # admits Poisson arrivals
+            n_live = int(live.sum())
+            newq = []
+            while pending and n_live + len(newq) < in_flight and (not realtime or now >= next_arrival):
+                newq.append(pending.popleft())
                 if realtime:
                     next_arrival += rng.exponential(1.0 / arrival_rate)
-            # closed loop / real time: submit next chunks of reads whose result came back
-            for lv in live.values():
-                if lv.ticket is None and (not realtime or now >= lv.next_ready):
-                    self._submit(lv, now)
-            B.rawalign_dtw_flush(self.al.h)
-            # collect results
-            done_ids = []
-            for rid, lv in live.items():
-                if lv.ticket is None:
-                    continue
-                res = B.rawalign_dtw_poll(self.al.h, lv.ticket, 64, timeout_us=-1)
-                t = time.perf_counter()
-                st.latencies_ms.append((t - lv.t_submit) * 1e3)
-                st.chunks += 1
-                st.cells += int(res["cells"].sum()) if len(res) else 0
-                lv.ticket = None
-                lv.next_ready = lv.t_submit + chunk_s
-                if self._decide(lv, res, st):
-                    done_ids.append(rid)
-            for rid in done_ids:
-                lv = live.pop(rid)
-                st.reads_done += 1
-                if lv.pos < min(self.max_events, len(lv.rd.events)):
-                    closed.append(B.rawalign_dtw_submit_chunk(self.al.h, rid, np.zeros(0, np.float32), None, True))
-            if closed:
-                B.rawalign_dtw_flush(self.al.h)
-                for t in closed:
-                    B.rawalign_dtw_poll(self.al.h, t, 0, timeout_us=-1)
-                closed = []
-            if realtime:
-                waits = [lv.next_ready for lv in live.values() if lv.ticket is None]
-                nxt = min(waits + ([next_arrival] if pending_reads else []), default=now)
-                dt = nxt - time.perf_counter()
+            if newq:
+                newq = np.array(newq, np.int64)
+                live[newq] = True
+                ready_at[newq] = now
+            # the reads whose next chunk can go now: in closed loop at most one
+            # generation's worth, and only while fewer generations are in flight
+            q = np.nonzero(live & ~busy & (ready_at <= now))[0]
+            if not realtime:
+                q = q[:gen_cap] if len(gens) < generations else q[:0]
+            closes = np.array(to_close, np.int64)
+            to_close = []
+            if len(q) or len(closes):
+                ch = np.concatenate([self._chunks(q, pos[q], False), self._chunks(closes, pos[closes], True)])
+                a = time.perf_counter()
+                tickets, status = B.rawalign_dtw_submit_chunks(h, ch, self.events, self.cands)
+                t_sub += time.perf_counter() - a
+                sq = status[: len(q)]
+                bad = np.concatenate([sq[(sq != B.RA_OK) & (sq != B.RA_EAGAIN)], status[len(q):][status[len(q):] != 0]])
+                if len(bad):
+                    raise B.RawAlignError("rawalign_dtw_submit_chunks", int(bad[0]))
+                # reads refused admission (no slot or arena memory) wait in front
+                refused = q[sq == B.RA_EAGAIN]
+                live[refused] = False
+                pending.extendleft(reversed(refused.tolist()))
+                ok = sq == B.RA_OK
+                qs = q[ok]
+                busy[qs] = True
+                pos[qs] += ch["n_events"][: len(q)][ok].astype(np.int64)
+                a = time.perf_counter()
+                B.rawalign_dtw_flush(h)
+                t_flush += time.perf_counter() - a
+                st.flushes += 1
+                gens.append((tickets[: len(q)][ok], qs, time.perf_counter(), tickets[len(q):]))
+            # read back the oldest generation: in closed loop when the others
+            # are on the GPU (or nothing else can start), in real time as soon
+            # as it has completed
+            while gens:
+                tk, qs, ts, ctk = gens[0]
+                must = (not realtime) and (len(gens) >= generations or not np.any(live & ~busy))
+                a = time.perf_counter()
+                got = B.rawalign_dtw_poll_chunks(h, np.concatenate([tk, ctk]), int(self.n_cand[qs].sum()) + 1,
+                                                 timeout_us=-1 if must else 0)
+                t_poll += time.perf_counter() - a
+                if got is None:
+                    break
+                gens.popleft()
+                res, counts = got
+                tv = time.perf_counter()
+                counts = counts[: len(tk)].astype(np.int64)
+                st.latencies_ms.append(np.full(len(tk), (tv - ts) * 1e3))
+                st.chunks += len(tk)
+                st.cells += int(res["cells"].sum())
+                # a chunk's results carry its read's decision (every candidate the same)
+                starts = np.cumsum(counts) - counts
+                dec = np.full(len(tk), B.RA_PENDING, np.int64)
+                has = counts > 0
+                dec[has] = res["decision"][starts[has]]
+                busy[qs] = False
+                ready_at[qs] = ts + chunk_s if realtime else tv
+                at_end = pos[qs] >= self.n_ev[qs]
+                acc = dec == B.RA_MAPPED
+                rej = (dec == B.RA_UNMAPPED) & ~at_end
+                exh = at_end & ~acc
+                done = acc | rej | exh
+                st.accepted += int(acc.sum())
+                st.rejected += int(rej.sum())
+                st.exhausted += int(exh.sum())
+                st.reads_done += int(done.sum())
+                live[qs[done]] = False
+                # decided before their last chunk: closed in the next round
+                to_close.extend(qs[done & ~at_end].tolist())
+                if must:
+                    break
+            if realtime and not gens and not to_close:
+                waits = ready_at[live & ~busy]
+                cands_t = ([float(waits.min())] if len(waits) else []) + ([next_arrival] if pending else [])
+                dt = (min(cands_t) if cands_t else now) - time.perf_counter()
                 if dt > 0:
-                    time.sleep(min(dt, 0.005))
+                    time.sleep(min(dt, 0.002))
         st.wall_s = time.perf_counter() - t0
-        # close whatever is still open so the library frees it
-        for rid, lv in live.items():
-            if lv.ticket is not None:
-                B.rawalign_dtw_poll(self.al.h, lv.ticket, 64, timeout_us=-1)
-            if lv.pos < min(self.max_events, len(lv.rd.events)):
-                t = B.rawalign_dtw_submit_chunk(self.al.h, rid, np.zeros(0, np.float32), None, True)
-                B.rawalign_dtw_flush(self.al.h)
-                B.rawalign_dtw_poll(self.al.h, t, 0, timeout_us=-1)
+        # drain: results still in flight, then close every read left open
+        while gens:
+            tk, qs, ts, ctk = gens.popleft()
+            B.rawalign_dtw_poll_chunks(h, np.concatenate([tk, ctk]), int(self.n_cand[qs].sum()) + 1)
+            busy[qs] = False
+        open_q = sorted(set(to_close) | set(np.nonzero(live & (pos > 0) & (pos < self.n_ev))[0].tolist()))
+        if open_q:
+            open_q = np.array(open_q, np.int64)
+            tickets, status = B.rawalign_dtw_submit_chunks(h, self._chunks(open_q, pos[open_q], True),
+                                                           self.events, self.cands)
+            B.rawalign_dtw_flush(h)
+            B.rawalign_dtw_poll_chunks(h, tickets[status == B.RA_OK], 1)
+        lib = B.rawalign_dtw_serve_stats(h, reset=True)
+        st.host = {"python_submit": t_sub * 1e3, "python_flush": t_flush * 1e3, "python_poll_wait": t_poll * 1e3,
+                   "python_other": (st.wall_s - t_sub - t_flush - t_poll) * 1e3,
+                   "library_submit": lib.host_submit_ms, "library_flush_plan_launch": lib.host_flush_ms,
+                   "device_h2d": lib.h2d_ms, "device_kernels": lib.device_ms, "device_d2h": lib.d2h_ms,
+                   "flushes": float(lib.flushes)}
         return st
 
 

@@ -54,9 +54,14 @@ def _c_layout():
 #include "rawalign_dtw.h"
 #define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
 int main(void) {
-  printf("cand %zu\nres %zu\ncfg %zu\nstats %zu\nanchor %zu\n", sizeof(rawalign_candidate_t),
-         sizeof(rawalign_result_t), sizeof(rawalign_dtw_config_t), sizeof(rawalign_dtw_stats_t),
-         sizeof(rawalign_anchor_t));
+  printf("cand %zu\nres %zu\ncfg %zu\nstats %zu\nanchor %zu\nchunk %zu\nsstats %zu\n",
+         sizeof(rawalign_candidate_t), sizeof(rawalign_result_t), sizeof(rawalign_dtw_config_t),
+         sizeof(rawalign_dtw_stats_t), sizeof(rawalign_anchor_t), sizeof(rawalign_chunk_t),
+         sizeof(rawalign_dtw_serve_stats_t));
+  O(rawalign_chunk_t, read_id); O(rawalign_chunk_t, ev_offset); O(rawalign_chunk_t, n_events);
+  O(rawalign_chunk_t, cand_offset); O(rawalign_chunk_t, n_cands); O(rawalign_chunk_t, last);
+  O(rawalign_dtw_serve_stats_t, cells); O(rawalign_dtw_serve_stats_t, host_submit_ms);
+  O(rawalign_dtw_serve_stats_t, d2h_ms);
   O(rawalign_anchor_t, q); O(rawalign_anchor_t, t); O(rawalign_anchor_t, len);
   O(rawalign_candidate_t, read_id); O(rawalign_candidate_t, ref_offset); O(rawalign_candidate_t, ref_len_bases);
   O(rawalign_candidate_t, strand); O(rawalign_candidate_t, band_w); O(rawalign_candidate_t, slope_num);
@@ -66,7 +71,7 @@ int main(void) {
   O(rawalign_result_t, is_best); O(rawalign_result_t, decision);
   O(rawalign_dtw_config_t, arena_dev); O(rawalign_dtw_config_t, arena_bytes); O(rawalign_dtw_config_t, cuda_stream);
   O(rawalign_dtw_config_t, max_candidates); O(rawalign_dtw_config_t, kernel); O(rawalign_dtw_config_t, autotune_path);
-  O(rawalign_dtw_config_t, early_termination);
+  O(rawalign_dtw_config_t, early_termination); O(rawalign_dtw_config_t, serve_early_reject);
   return 0;
 }
 """
@@ -86,12 +91,20 @@ def test_record_layouts_agree():
     assert int(lay["cfg"]) == C.sizeof(B.Config)
     assert int(lay["stats"]) == C.sizeof(B.Stats)
     assert int(lay["anchor"]) == B.ANCHOR_DTYPE.itemsize == S.ANCHOR_DTYPE.itemsize == C.sizeof(O.Anchor) == 12
+    assert int(lay["chunk"]) == B.CHUNK_DTYPE.itemsize == 32
+    assert int(lay["sstats"]) == C.sizeof(B.ServeStats)
     for k, v in lay.items():
         if "." not in k:
             continue
         T, f = k.split(".")
         if T == "rawalign_anchor_t":
             assert S.ANCHOR_DTYPE.fields[f][1] == int(v) == getattr(O.Anchor, f).offset, k
+            continue
+        if T == "rawalign_chunk_t":
+            assert B.CHUNK_DTYPE.fields[f][1] == int(v), k
+            continue
+        if T == "rawalign_dtw_serve_stats_t":
+            assert getattr(B.ServeStats, f).offset == int(v), k
             continue
         py = {"rawalign_candidate_t": B.Candidate, "rawalign_result_t": B.Result, "rawalign_dtw_config_t": B.Config}[T]
         assert getattr(py, f).offset == int(v), k

@@ -38,9 +38,48 @@ def _oracle_prefix(pore, ref, ref_len, cand, ev_prefix, b_match=0.4):
     return cost, O.score_f32(b_match, len(ev_prefix), cost), ei, ej
 
 
-def _aligner(pore, ref, ref_len, slots=64, arena=256 << 20, max_events=4000):
+def _aligner(pore, ref, ref_len, slots=64, arena=256 << 20, max_events=4000, early_reject=False):
     return B.Aligner(pore, ref, ref_len, arena_bytes=arena, serve_slots=slots, serve_max_events=max_events,
-                     max_candidates=32)
+                     max_candidates=32, serve_early_reject=early_reject)
+
+
+def _flat(reads):
+    """Every read's events and candidates back to back, for submit_chunks."""
+    ev_off = np.zeros(len(reads) + 1, np.int64)
+    ev_off[1:] = np.cumsum([len(rd.events) for rd in reads])
+    c_off = np.zeros(len(reads) + 1, np.int64)
+    c_off[1:] = np.cumsum([len(rd.cands) for rd in reads])
+    return (np.concatenate([rd.events for rd in reads]).astype(np.float32), ev_off,
+            np.concatenate([rd.cands for rd in reads]), c_off)
+
+
+def _run_reads_batched(al, reads, chunk=180):
+    """As _run_reads with fixed chunks, but every round is one submit_chunks
+    call, one flush and one poll_chunks call."""
+    ev, ev_off, cands, c_off = _flat(reads)
+    out = {rd.read_id: [] for rd in reads}
+    pos = np.zeros(len(reads), np.int64)
+    lens = np.array([len(rd.events) for rd in reads], np.int64)
+    while np.any(pos < lens):
+        q = np.nonzero(pos < lens)[0]
+        ch = np.zeros(len(q), B.CHUNK_DTYPE)
+        stop = np.minimum(pos[q] + chunk, lens[q])
+        ch["read_id"] = [reads[x].read_id for x in q]
+        ch["ev_offset"] = ev_off[q] + pos[q]
+        ch["n_events"] = stop - pos[q]
+        ch["cand_offset"] = np.where(pos[q] == 0, c_off[q], 0)
+        ch["n_cands"] = np.where(pos[q] == 0, c_off[q + 1] - c_off[q], 0)
+        ch["last"] = stop >= lens[q]
+        tickets, status = B.rawalign_dtw_submit_chunks(al.h, ch, ev, cands)
+        assert np.all(status == B.RA_OK) and np.all(tickets > 0)
+        B.rawalign_dtw_flush(al.h)
+        res, counts = B.rawalign_dtw_poll_chunks(al.h, tickets, int(c_off[-1]))
+        at = 0
+        for x, n in zip(q, counts):
+            out[reads[x].read_id].append((int(stop[list(q).index(x)]), res[at:at + n]))
+            at += n
+        pos[q] = stop
+    return out
 
 
 def _run_reads(al, reads, chunk_sizes, rng_chunks=None):
@@ -192,7 +231,7 @@ def test_request_loop_closed_and_realtime():
         st = ServingLoop(al, reads, max_events=1200).run(max_chunks=10 ** 6, in_flight=16)
         assert st.reads_done == len(reads)
         assert st.accepted + st.rejected + st.exhausted == st.reads_done
-        assert st.chunks == len(st.latencies_ms) and st.cells > 0
+        assert st.chunks == sum(len(x) for x in st.latencies_ms) and st.cells > 0
         on = sum(rd.on_target for rd in reads)
         assert st.accepted >= on * 0.8
         rt = ServingLoop(al, reads[:8], max_events=1200).run(max_chunks=10 ** 6, in_flight=8, realtime=True,
@@ -228,3 +267,110 @@ def test_decision_policy_study():
     assert acc == sorted(acc, reverse=True) and rej == sorted(rej)
     assert all(st[t]["accepted"] + st[t]["rejected"] + st[t]["undecided"] == len(reads) for t in thresholds)
     assert st[20.0]["accepted"] > 0 and st[20.0]["precision"] >= 0.9
+
+
+def test_batched_submit_and_poll_equal_one_by_one():
+    """submit_chunks / poll_chunks give, chunk for chunk, the results of one
+    submit_chunk / poll per chunk, and those equal the oracle's prefix DTW."""
+    pore, ref, ref_len, reads = _serving_inputs(n_reads=10, max_events=700, seed=41)
+    al = _aligner(pore, ref, ref_len)
+    try:
+        one = _run_reads(al, reads, [180])
+    finally:
+        al.close()
+    al = _aligner(pore, ref, ref_len)
+    try:
+        many = _run_reads_batched(al, reads)
+        stats = B.rawalign_dtw_serve_stats(al.h)
+    finally:
+        al.close()
+    cells = 0
+    for rd in reads:
+        assert [q for q, _ in one[rd.read_id]] == [q for q, _ in many[rd.read_id]]
+        for (_, a), (_, b) in zip(one[rd.read_id], many[rd.read_id]):
+            for f in a.dtype.names:
+                assert np.array_equal(a[f], b[f]), f
+            cells += int(b["cells"].sum())
+    _check_against_oracle(pore, ref, ref_len, reads[:3], many)
+    assert stats.flushes == 4 and stats.chunks == 40 and stats.cells == cells
+    assert stats.device_ms > 0 and stats.h2d_ms >= 0 and stats.d2h_ms >= 0
+
+
+def test_poll_chunks_refuses_without_consuming():
+    pore, ref, ref_len, reads = _serving_inputs(n_reads=2, max_events=360, seed=43)
+    al = _aligner(pore, ref, ref_len)
+    try:
+        t0 = B.rawalign_dtw_submit_chunk(al.h, reads[0].read_id, reads[0].events[:180], reads[0].cands, False)
+        t1 = B.rawalign_dtw_submit_chunk(al.h, reads[1].read_id, reads[1].events[:180], reads[1].cands, False)
+        # queued, not flushed: not ready (waiting would not help)
+        assert B.rawalign_dtw_poll_chunks(al.h, [t0], 64, timeout_us=-1) is None
+        B.rawalign_dtw_flush(al.h)
+        need = len(reads[0].cands) + len(reads[1].cands)
+        for bad in ([t0, t1, t0], [t0, 12345678], [t0, t1]):
+            with pytest.raises(B.RawAlignError) as ei:
+                B.rawalign_dtw_poll_chunks(al.h, bad, need if len(bad) != 2 or bad[1] != t1 else need - 1)
+            assert ei.value.code == B.RA_EINVAL
+        res, counts = B.rawalign_dtw_poll_chunks(al.h, [t1, t0], need)
+        assert list(counts) == [len(reads[1].cands), len(reads[0].cands)]
+        assert np.all(res["read_id"][: counts[0]] == reads[1].read_id)
+        with pytest.raises(B.RawAlignError):
+            B.rawalign_dtw_poll_chunks(al.h, [t0], need)  # consumed
+    finally:
+        al.close()
+
+
+def test_early_reject_decision():
+    """With serve_early_reject a chunk before the last is decided UNMAPPED
+    exactly when, for every candidate, fl(fl(B_Match * max_events) - cost)
+    is below Score_Threshold (FP32, as the score): no later chunk can map
+    the read.  Otherwise MAPPED when the best score reaches the threshold,
+    else PENDING."""
+    max_ev = 540
+    pore, ref, ref_len, reads = _serving_inputs(n_reads=16, max_events=max_ev, seed=47)
+    al = _aligner(pore, ref, ref_len, max_events=max_ev, early_reject=True)
+    try:
+        got = _run_reads_batched(al, reads)
+    finally:
+        al.close()
+    _check_against_oracle(pore, ref, ref_len, reads[:4], got)
+    xb = np.float32(0.4) * np.float32(max_ev)
+    kinds = set()
+    for rd in reads:
+        for q, res in got[rd.read_id]:
+            dec = set(res["decision"].tolist())
+            assert len(dec) == 1
+            dec = dec.pop()
+            if q == len(rd.events):
+                assert dec in (B.RA_MAPPED, B.RA_UNMAPPED)
+                continue
+            if np.max(res["score"]) >= np.float32(20.0):
+                want = B.RA_MAPPED
+            elif np.all((xb - res["cost"]).astype(np.float32) < np.float32(20.0)):
+                want = B.RA_UNMAPPED
+            else:
+                want = B.RA_PENDING
+            assert dec == want, (rd.read_id, q)
+            kinds.add(want)
+    assert B.RA_UNMAPPED in kinds and B.RA_PENDING in kinds
+
+
+def test_serving_loop_with_early_reject():
+    """The request loop with the library's reject decision: every read is
+    accepted, rejected before its end or runs to max_events; rejects happen
+    for off-target reads; the counters add up."""
+    from paper_2310_05037_gb300.serving import ServingLoop
+
+    pore, ref, ref_len, reads = _serving_inputs(n_reads=48, max_events=1080, seed=53)
+    al = _aligner(pore, ref, ref_len, slots=16, max_events=1080, early_reject=True)
+    try:
+        st = ServingLoop(al, reads, max_events=1080).run(max_chunks=10 ** 6, in_flight=16)
+        assert st.reads_done == len(reads)
+        assert st.accepted + st.rejected + st.exhausted == st.reads_done
+        assert st.rejected > 0 and st.accepted >= 0.8 * sum(rd.on_target for rd in reads)
+        summ = st.summary()
+        assert summ["chunks"] == st.chunks > 0 and summ["breakdown_ms"]["device_kernels"] > 0
+        # every slot and block came back: a fresh batch of the same reads is admitted again
+        st2 = ServingLoop(al, reads[:16], max_events=1080).run(max_chunks=10 ** 6, in_flight=16)
+        assert st2.reads_done == 16
+    finally:
+        al.close()
