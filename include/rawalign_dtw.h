@@ -297,8 +297,13 @@ int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_events, const f
  * number of variants, 10: same order as RA_KERNEL_VARIANT0 + v).  The planner
  * picks, per alignment, the variant with the fewest cost-weighted slots; the
  * autotuner measures these costs.  config.autotune_path may name a text file
- * of "G HR cost" lines with the same numbers.  Returns RA_EINVAL for a wrong
- * count or a non-positive cost. */
+ * of "G HR cost" lines with the same numbers, and the planner's bin edges:
+ * "ring_bins S" (S = 2: launch classes bin ring sizes by powers of four, the
+ * default; S = 1: by powers of two) and "latency_split X" (an alignment
+ * longer than X times the batch's estimated length moves to a 32-lane
+ * variant; 0 = automatic); create returns RA_EINVAL for other values.  None
+ * of these change results, only the launch plan.  Returns RA_EINVAL for a
+ * wrong count or a non-positive cost. */
 int rawalign_dtw_set_variant_costs(rawalign_dtw_t *h, const double *costs, uint32_t n);
 
 /* Anchor-guided batch (Sec. 2.4.2): as rawalign_dtw_prepare_batch, but each

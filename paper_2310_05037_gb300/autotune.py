@@ -1,18 +1,29 @@
-"""Autotuner for the striped DTW kernel's variants.
+"""Autotuner for the striped DTW kernel and its planner.
 
-Each variant (lanes per alignment G, rows per lane HR) is timed on a batch
-made for it: alignments whose band is just wide enough that the variant's
-lanes never wait between stripes (2w >= (G*HR - HR + 1) + G + 4 columns at
-slope 1), about four stripes long, and enough of them to keep every resident
-group busy several times over.  The measured lane-cell slots per second of
-each variant give its relative slot cost (1.0 = the fastest); the planner
-picks, per alignment, the variant with the fewest cost-weighted slots.
+Slot costs: each variant (lanes per alignment G, rows per lane HR) is timed on
+a batch made for it: alignments whose band is just wide enough that the
+variant's lanes never wait between stripes, about four stripes long, and
+enough of them to keep every resident group busy several times over.  The
+measured lane-cell slots per second of each variant give its relative slot
+cost (1.0 = the fastest); the planner picks, per alignment, the variant with
+the fewest cost-weighted slots.
 
-    costs = tune()                      # {(G, HR): cost}
-    write_table("tune.txt", costs)      # "G HR cost" lines
+Bin edges: the planner cuts a batch into launch classes of one variant and
+one ring size (the ring holds the bottom row of a stripe for the next one, so
+its size follows the band width), and moves an alignment that would outlast
+the batch to a 32-lane variant.  tune_plan() times a sample batch under each
+choice of ring-size bins (powers of 4 or of 2) and of that latency split and
+keeps the fastest.
+
+    costs = tune()                                  # {(G, HR): cost}
+    plan = tune_plan(sample_workload, costs)[0]     # {"ring_bins": s, "latency_split": x}
+    write_table("tune.txt", costs, plan)            # "G HR cost" lines + knobs
     Aligner(..., autotune_path="tune.txt")
 """
 from __future__ import annotations
+
+import os
+import tempfile
 
 import numpy as np
 
@@ -41,7 +52,7 @@ def calibration_batch(G, HR, n_align, seed=0):
     return pore, ref, ref_len, events, offs, cands
 
 
-def tune(device="cuda:0", runs=3, sm_count=None, groups_factor=4, verbose=False):
+def tune(device="cuda:0", runs=3, sm_count=None, groups_factor=4, verbose=False, variants=None):
     """Returns {(G, HR): relative slot cost} measured on this GPU."""
     import torch
 
@@ -49,6 +60,8 @@ def tune(device="cuda:0", runs=3, sm_count=None, groups_factor=4, verbose=False)
         sm_count = torch.cuda.get_device_properties(torch.device(device)).multi_processor_count
     theta = {}
     for v, (G, HR) in enumerate(B.VARIANTS):
+        if variants is not None and (G, HR) not in variants:
+            continue
         # resident groups: about 5 blocks of 128 threads per SM
         n_align = max(64, sm_count * 5 * (128 // G) * groups_factor // 4)
         pore, ref, ref_len, ev, offs, cands = calibration_batch(G, HR, n_align, seed=v)
@@ -75,21 +88,67 @@ def tune(device="cuda:0", runs=3, sm_count=None, groups_factor=4, verbose=False)
     return {gh: top / t for gh, t in theta.items()}
 
 
-def write_table(path, costs):
+def tune_plan(workload, costs=None, device="cuda:0", runs=3, ring_bins=(2, 1), latency_splits=(0.0, 0.5, 1.0, 2.0),
+              arena_bytes=None):
+    """Chooses the planner's bin edges on a sample batch (a synth.Workload):
+    every (ring_bins, latency_split) pair is timed (best of `runs` replays of
+    the DTW part); returns (best {"ring_bins", "latency_split"}, {pair: ms})."""
+    w = workload
+    if arena_bytes is None:
+        m_total = int(np.sum(w.cands["ref_len_bases"].astype(np.int64) - w.k + 1))
+        arena_bytes = 2 * B.rawalign_dtw_batch_bytes(len(w.events), w.n_reads, w.n_cands, m_total) + \
+            len(w.ref2bit) + (512 << 20)
+    times = {}
+    with tempfile.TemporaryDirectory() as d:
+        for rb in ring_bins:
+            for ls in latency_splits:
+                path = os.path.join(d, "t_%d_%g.txt" % (rb, ls))
+                write_table(path, costs or {}, {"ring_bins": rb, "latency_split": ls})
+                al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena_bytes, k=w.k, device=device,
+                               autotune_path=path)
+                try:
+                    b = al.prepare(w.events, w.read_offsets, w.cands)
+                    al.poll(al.run(b), 0)
+                    best = None
+                    for _ in range(runs):
+                        al.poll(al.run(b), 0)
+                        ms = al.stats(b).dtw_ms
+                        best = ms if best is None else min(best, ms)
+                    times[(rb, ls)] = best
+                    al.release(b)
+                finally:
+                    al.close()
+    (rb, ls) = min(times, key=times.get)
+    return {"ring_bins": rb, "latency_split": ls}, times
+
+
+def write_table(path, costs, plan=None):
+    """The tuning file: "G HR cost" lines, then the planner knobs."""
     with open(path, "w") as f:
         for (G, HR), c in costs.items():
             f.write("%d %d %.6f\n" % (G, HR, c))
+        if plan:
+            if "ring_bins" in plan:
+                f.write("ring_bins %d\n" % int(plan["ring_bins"]))
+            if "latency_split" in plan:
+                f.write("latency_split %.6f\n" % float(plan["latency_split"]))
 
 
 def read_table(path):
-    costs = {}
+    """(costs {(G, HR): cost}, plan knobs {name: value}) from a tuning file."""
+    costs, plan = {}, {}
     for line in open(path):
         parts = line.split()
         if len(parts) == 3:
             costs[(int(parts[0]), int(parts[1]))] = float(parts[2])
-    return costs
+        elif len(parts) == 2 and parts[0] == "ring_bins":
+            plan["ring_bins"] = int(parts[1])
+        elif len(parts) == 2 and parts[0] == "latency_split":
+            plan["latency_split"] = float(parts[1])
+    return costs, plan
 
 
 def apply(aligner, costs):
-    """Sets the measured costs on an open Aligner."""
+    """Sets the measured slot costs on an open Aligner (the planner knobs
+    come only from a tuning file given at creation)."""
     B.rawalign_dtw_set_variant_costs(aligner.h, [costs.get(gh, 1.0) for gh in B.VARIANTS])

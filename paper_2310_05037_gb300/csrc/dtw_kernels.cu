@@ -279,14 +279,31 @@ __global__ void decide_kernel(rawalign_result_t *res, int n, const unsigned long
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+
+// SMs of the current device (queried once per device): grid-stride launches
+// are capped at a few resident blocks per SM.
+static int device_sms()
+{
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return 152;
+    if (sms[dev] <= 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            return 152;
+        sms[dev] = n;
+    }
+    return sms[dev];
+}
 cudaError_t launch_expected_signal(const SigDesc *d, int n, const uint8_t *ref2bit, const float *pore,
                                    int k, float *r_all, cudaStream_t s)
 {
     if (n <= 0)
         return cudaSuccess;
     int blocks = (n + 7) / 8;
-    if (blocks > 152 * 8)
-        blocks = 152 * 8;
+    if (blocks > device_sms() * 8)
+        blocks = device_sms() * 8;
     const uint32_t *ref32 = (const uint32_t *)ref2bit;  // 256-byte aligned, padded by 16 bytes
     if (k <= 6) {
         expected_signal_kernel<true><<<blocks, 256, sizeof(float) << (2 * k), s>>>(d, n, ref32, pore, k, r_all);
@@ -303,8 +320,8 @@ cudaError_t launch_combine(const CombineDesc *d, int n, const PieceRef *plan, co
     if (n <= 0)
         return cudaSuccess;
     int blocks = (n + 127) / 128;
-    if (blocks > 152 * 16)
-        blocks = 152 * 16;
+    if (blocks > device_sms() * 16)
+        blocks = device_sms() * 16;
     combine_kernel<<<blocks, 128, 0, s>>>(d, n, plan, pieces, events, r_all, results, best_keys, b_match);
     return cudaGetLastError();
 }
@@ -314,8 +331,8 @@ cudaError_t launch_check_events(const float *ev, uint64_t n, int *err, cudaStrea
     if (n == 0)
         return cudaSuccess;
     uint64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 8)
-        blocks = 152 * 8;
+    if (blocks > (uint64_t)device_sms() * 8)
+        blocks = device_sms() * 8;
     check_events_kernel<<<(unsigned)blocks, 256, 0, s>>>(ev, n, err);
     return cudaGetLastError();
 }
@@ -342,8 +359,8 @@ cudaError_t launch_decide(rawalign_result_t *results, int n, const unsigned long
     if (n <= 0)
         return cudaSuccess;
     int blocks = (n + 255) / 256;
-    if (blocks > 152 * 8)
-        blocks = 152 * 8;
+    if (blocks > device_sms() * 8)
+        blocks = device_sms() * 8;
     decide_kernel<<<blocks, 256, 0, s>>>(results, n, best_keys, read_of, thr, final_decision);
     return cudaGetLastError();
 }

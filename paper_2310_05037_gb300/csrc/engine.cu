@@ -275,7 +275,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
                 }
             }
             it.wave = 0;
-            set_schedule(it, sc);
+            set_schedule(it, sc, h->plan.ring_bin_shift);
             pt_.max_rows = std::max<int>(pt_.max_rows, (int)n);
         };
         uint64_t ix = pt_.ib, px = pt_.pb, rx = pt_.rb;
@@ -351,7 +351,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
         b.max_rows = std::max(b.max_rows, pt_.max_rows);
     uint64_t slots[kNumVariants];
     if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO)
-        shorten_longest(items, n_items, h->sm_count, h->slot_cost, slots);
+        shorten_longest(items, n_items, h->sm_count, h->slot_cost, slots, h->plan);
     else
         variant_slots(items, n_items, slots);
     b.slots = 0;
@@ -581,19 +581,39 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
     for (int v = 0; v < kNumVariants; ++v)
         h->slot_cost[v] = kSlotCost[v];
     if (config->autotune_path) {
-        // lines "G HR cost": the measured relative cost of one lane-cell slot
+        // lines "G HR cost": the measured relative cost of one lane-cell
+        // slot; "ring_bins S" and "latency_split X": the planner's knobs
         FILE *f = fopen(config->autotune_path, "r");
         if (!f) {
             delete h;
             return RA_EINVAL;
         }
-        int G, HR;
-        double c;
-        while (fscanf(f, "%d %d %lf", &G, &HR, &c) == 3)
-            for (int v = 0; v < kNumVariants; ++v)
-                if (kVariants[v][0] == G && kVariants[v][1] == HR && c > 0 && std::isfinite(c))
-                    h->slot_cost[v] = c;
+        char line[256];
+        bool bad = false;
+        while (fgets(line, sizeof line, f)) {
+            int G, HR, sh;
+            double c;
+            if (sscanf(line, "%d %d %lf", &G, &HR, &c) == 3) {
+                for (int v = 0; v < kNumVariants; ++v)
+                    if (kVariants[v][0] == G && kVariants[v][1] == HR && c > 0 && std::isfinite(c))
+                        h->slot_cost[v] = c;
+            } else if (sscanf(line, " ring_bins %d", &sh) == 1) {
+                if (sh == 1 || sh == 2)
+                    h->plan.ring_bin_shift = sh;
+                else
+                    bad = true;
+            } else if (sscanf(line, " latency_split %lf", &c) == 1) {
+                if (std::isfinite(c) && c >= 0)
+                    h->plan.latency_split = c;
+                else
+                    bad = true;
+            }
+        }
         fclose(f);
+        if (bad) {
+            delete h;
+            return RA_EINVAL;
+        }
     }
     h->cfg.autotune_path = nullptr;
     h->stream = (cudaStream_t)config->cuda_stream;
@@ -642,6 +662,7 @@ extern "C" int rawalign_dtw_prepare_batch(rawalign_dtw_t *h, const float *events
                                           uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
                                           uint64_t *batch)
 {
+    NvtxRange nvtx_range("rawalign_dtw_prepare_batch");
     if (!h || !batch || !read_offsets || (n_cands && !cands) || (!events && n_reads))
         return RA_EINVAL;
     cudaSetDevice(h->device);
@@ -662,6 +683,7 @@ extern "C" int rawalign_dtw_prepare_anchored(rawalign_dtw_t *h, const float *eve
                                              const rawalign_anchor_t *anchors, const uint64_t *anchor_offsets,
                                              uint64_t *batch)
 {
+    NvtxRange nvtx_range("rawalign_dtw_prepare_anchored");
     if (!h || !batch || !read_offsets || !anchor_offsets || (n_cands && !cands) || (!events && n_reads))
         return RA_EINVAL;
     cudaSetDevice(h->device);
@@ -682,6 +704,7 @@ extern "C" int rawalign_dtw_submit_anchored(rawalign_dtw_t *h, const float *even
                                             const rawalign_anchor_t *anchors, const uint64_t *anchor_offsets,
                                             uint64_t *ticket)
 {
+    NvtxRange nvtx_range("rawalign_dtw_submit_anchored");
     if (!ticket)
         return RA_EINVAL;
     uint64_t bid = 0;
@@ -702,6 +725,7 @@ extern "C" int rawalign_dtw_submit_anchored(rawalign_dtw_t *h, const float *even
 
 extern "C" int rawalign_dtw_run_batch(rawalign_dtw_t *h, uint64_t batch, uint64_t *ticket)
 {
+    NvtxRange nvtx_range("rawalign_dtw_run_batch");
     if (!h || !ticket)
         return RA_EINVAL;
     auto it = h->batches.find(batch);
@@ -736,6 +760,7 @@ extern "C" int rawalign_dtw_submit_batch(rawalign_dtw_t *h, const float *events,
                                          uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
                                          uint64_t *ticket)
 {
+    NvtxRange nvtx_range("rawalign_dtw_submit_batch");
     if (!ticket)
         return RA_EINVAL;
     uint64_t bid = 0;
@@ -756,6 +781,7 @@ extern "C" int rawalign_dtw_submit_batch(rawalign_dtw_t *h, const float *events,
 extern "C" int rawalign_dtw_poll(rawalign_dtw_t *h, uint64_t ticket, rawalign_result_t *out, uint32_t cap,
                                  uint32_t *n_out, int64_t timeout_us)
 {
+    NvtxRange nvtx_range("rawalign_dtw_poll");
     if (!h || !n_out || (cap && !out))
         return RA_EINVAL;
     *n_out = 0;

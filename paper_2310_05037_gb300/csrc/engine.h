@@ -17,13 +17,26 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 using namespace ra;
 
 namespace ra_host {
 
+// An NVTX range around one entry point (submit, plan, launch, poll), so that
+// a profiler's timeline shows where the host time goes; without a profiler
+// attached the calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 constexpr int kBlock = 128;
+constexpr int kLag = ra::kLaneLag;  // columns between neighbouring lanes (the kernel's)
 // (lanes per alignment, rows per lane); the cost factor is the relative issue
 // cost of one lane-cell slot (more rows per lane amortise the per-step work).
 // Relative cost of one lane-cell slot per variant: the autotuner's
@@ -203,7 +216,12 @@ inline int band_for(int64_t n, int64_t m, int32_t band_w, int64_t num_in, int64_
 // the last in-band column of a lane's rows in stripe k and a the first of its
 // rows in stripe k+1.  With hi(x) <= x*s + w and lo(y) >= y*s - w
 // (s = num/den, y - x = H - HR + 1): b - a <= 2w - (H - HR + 1) s, and
-// b - a <= m - 1 from the table's edges.
+// b - a <= m - 1 from the table's edges.  Lane t runs kLag columns behind lane
+// t-1 (it takes lane t-1's bottom row from kLag steps back, so the kernel can
+// compute two consecutive columns of a lane as two interleaved chains); the
+// last lane of a stripe writes a ring entry kLag * (G-1) steps after lane 0
+// passed its column, and lane 0 of the next stripe may read it two steps
+// before it uses it, two steps after it is written: dC >= kLag * G + 3.
 struct Sched {
     int32_t dC = 0, a0 = 0, s_end = 0;
     double cells_est = 0;
@@ -223,12 +241,12 @@ inline Sched schedule(const BandDef &b, int64_t row0, int64_t nrows, int G, int 
     }
     int64_t span = fdiv(2 * b.w * b.den - (H - HR + 1) * b.num, b.den);
     span = std::min<int64_t>(span, b.m - 1);
-    const int64_t dC = std::max<int64_t>(G + 1, span + 2);
+    const int64_t dC = std::max<int64_t>((int64_t)kLag * G + 3, span + 2);
     const int64_t nl = nrows - 1 - (K - 1) * H;
     const int64_t t_last = nl / HR;
     const int64_t b_last = b.hi(last);
     s.dC = (int32_t)dC;
-    const int64_t se = b_last - s.a0 + 3 + t_last + (K - 1) * dC;
+    const int64_t se = b_last - s.a0 + 3 + (int64_t)kLag * t_last + (K - 1) * dC;
     s.s_end = (int32_t)std::max<int64_t>(se, 1);
     s.cells_est = (double)nrows * (double)std::min<int64_t>(2 * b.w + 1, b.m);
     const double slots = (double)s.s_end * G * HR;
@@ -365,6 +383,16 @@ struct SortScratch {
 
 struct ServeState;
 
+// Planner knobs the autotuner may set (tuning file lines "ring_bins S" and
+// "latency_split X"): launch classes bin ring sizes by powers of 2^S, and
+// an alignment longer than X times the estimated batch length moves to a
+// 32-lane variant (X <= 0: 0.5 for batches with few alignments per resident
+// group, else 1.0).
+struct PlanParams {
+    int ring_bin_shift = 2;
+    double latency_split = 0;
+};
+
 }  // namespace ra_host
 
 using namespace ra_host;
@@ -393,6 +421,7 @@ struct rawalign_dtw {
     int max_blocks[kNumVariants][2] = {};
     ServeState *serve = nullptr;       // Read-Until serving state (serve.cu)
     double slot_cost[kNumVariants] = {};  // relative cost of a lane-cell slot per variant
+    ra_host::PlanParams plan;             // planner knobs from the tuning file
 };
 
 
@@ -444,15 +473,15 @@ inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &o
     return best;
 }
 
-inline int ring_need(const WorkDesc &wd, int G);
+inline int ring_need(const WorkDesc &wd, int G, int bin_shift = 2);
 
-inline void set_schedule(PlanItem &it, const Sched &s)
+inline void set_schedule(PlanItem &it, const Sched &s, int bin_shift = 2)
 {
     it.wd.dC = s.dC;
     it.wd.a0 = s.a0;
     it.wd.s_end = s.s_end;
     it.cost = (double)s.s_end * kVariants[it.variant][0];
-    it.cap = ring_need(it.wd, kVariants[it.variant][0]);
+    it.cap = ring_need(it.wd, kVariants[it.variant][0], bin_shift);
 }
 
 // A batch lasts at least as long as its longest alignment on one group.  The
@@ -486,14 +515,15 @@ inline void variant_slots(const PlanItem *items, size_t n, uint64_t out[kNumVari
 }
 
 // slots: receives the lane-cell slots per variant after the pass.
-inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const double *cost, uint64_t slots[kNumVariants])
+inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const double *cost, uint64_t slots[kNumVariants],
+                            const PlanParams &pp = PlanParams())
 {
     variant_slots(items, n, slots);
     double total = 0;
     for (int v = 0; v < kNumVariants; ++v)
         total += (double)slots[v] * cost[v];
     const double groups = 32.0 * std::max(sm_count, 1);
-    const double theta = (double)n < 4.0 * groups ? 0.5 : 1.0;
+    const double theta = pp.latency_split > 0 ? pp.latency_split : ((double)n < 4.0 * groups ? 0.5 : 1.0);
     const double batch_len = theta * total / (512.0 * std::max(sm_count, 1));
     std::mutex mu;
     parallel_for(n, [&](uint64_t lo, uint64_t hi) {
@@ -528,7 +558,7 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
                 continue;
             moved[v0] -= (int64_t)it.wd.s_end * kVariants[v0][0] * kVariants[v0][1];
             it.variant = best;
-            set_schedule(it, best_s);
+            set_schedule(it, best_s, pp.ring_bin_shift);
             moved[best] += (int64_t)std::max(it.wd.s_end, 0) * kVariants[best][0] * kVariants[best][1];
             any = true;
         }
@@ -557,10 +587,10 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
     // neighbours in the queue should finish together.  With early termination
     // each bucket holds the reads' first candidates before the others.
     // Linear in the number of items and deterministic.
-    constexpr int kCaps = 12;  // ring sizes 128 << 2i
+    constexpr int kCaps = 24;  // ring sizes 128 << i
     auto cap_index = [](int cap) {
         int i = 0;
-        while (i < kCaps - 1 && (128ll << (2 * i)) < cap)
+        while (i < kCaps - 1 && (128ll << i) < cap)
             ++i;
         return i;
     };
@@ -582,15 +612,26 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
         }
     });
     if (n <= 16384) {
-        // small batches (serving flushes): a comparison sort of (key, index)
-        // pairs gives the same order without the radix passes' 64 K counters
-        std::vector<std::pair<uint64_t, int>> kv(n);
-        for (size_t x = 0; x < n; ++x)
-            kv[x] = {key[x], (int)x};
-        std::sort(kv.begin(), kv.end());
-        for (size_t x = 0; x < n; ++x) {
-            key[x] = kv[x].first;
-            ord[x] = kv[x].second;
+        // small batches (serving flushes): the same stable LSD radix sort with
+        // 8-bit digits on one thread, skipping the digits every key shares
+        uint64_t diff = 0;
+        for (size_t x = 1; x < n; ++x)
+            diff |= key[x] ^ key[0];
+        for (int shift = 0; shift < 64; shift += 8) {
+            if (((diff >> shift) & 0xFF) == 0)
+                continue;
+            uint32_t c8[257] = {};
+            for (size_t x = 0; x < n; ++x)
+                ++c8[((key[x] >> shift) & 0xFF) + 1];
+            for (int d = 0; d < 256; ++d)
+                c8[d + 1] += c8[d];
+            for (size_t x = 0; x < n; ++x) {
+                const uint32_t y = c8[(key[x] >> shift) & 0xFF]++;
+                key2[y] = key[x];
+                tmp[y] = ord[x];
+            }
+            std::swap(key, key2);
+            std::swap(ord, tmp);
         }
     }
     // each pass: per-chunk digit counts, offsets in (digit, chunk) order,
@@ -685,13 +726,14 @@ inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &o
 
 // Ring entries one piece needs: the stripe period plus two (written one step
 // before read) and room for the stored row above (serving).
-inline int ring_need(const WorkDesc &wd, int G)
+inline int ring_need(const WorkDesc &wd, int G, int bin_shift)
 {
-    int64_t need = std::max<int64_t>((int64_t)wd.dC + 2, (int64_t)wd.fin_wid + G + 2);
-    // sizes in powers of four (128, 512, 2048, ...): few launch classes
+    int64_t need = std::max<int64_t>((int64_t)wd.dC + 2, (int64_t)wd.fin_wid + (int64_t)kLag * G + 4);
+    // sizes in powers of 2^bin_shift (default four: 128, 512, 2048, ...):
+    // coarser bins give fewer launch classes, finer ones smaller rings
     int64_t cap = 128;
     while (cap < need)
-        cap <<= 2;
+        cap <<= bin_shift;
     return (int)cap;
 }
 

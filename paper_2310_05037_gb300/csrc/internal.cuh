@@ -11,6 +11,9 @@ namespace ra {
 
 constexpr float kInf = __builtin_huge_valf();
 constexpr int kBigCol = 0x3FFFFFFF;  // column index no band reaches: masks a row off
+// Columns by which lane t of a striped group trails lane t-1 (the planner's
+// schedule and the kernel must agree).
+constexpr int kLaneLag = 2;
 
 // One alignment, or one chunk of rows of one alignment (serving).
 // Rows are read events (global index row0 .. row0+nrows-1); columns are the

@@ -402,6 +402,7 @@ extern "C" int rawalign_dtw_submit_chunk(rawalign_dtw_t *h, uint64_t read_id, co
                                          const rawalign_candidate_t *cands, uint32_t n_cands, int last,
                                          uint64_t *ticket)
 {
+    NvtxRange nvtx_range("rawalign_dtw_submit_chunk");
     if (!h || !ticket || (n_events && !events))
         return RA_EINVAL;
     ServeState *st = state(h);
@@ -418,6 +419,7 @@ extern "C" int rawalign_dtw_submit_chunks(rawalign_dtw_t *h, const rawalign_chun
                                           const float *events, const rawalign_candidate_t *cands, uint64_t *tickets,
                                           int32_t *status)
 {
+    NvtxRange nvtx_range("rawalign_dtw_submit_chunks");
     if (!h || (n_chunks && (!chunks || !tickets || !status)))
         return RA_EINVAL;
     ServeState *st = state(h);
@@ -446,6 +448,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st);
 
 extern "C" int rawalign_dtw_flush(rawalign_dtw_t *h)
 {
+    NvtxRange nvtx_range("rawalign_dtw_flush");
     if (!h)
         return RA_EINVAL;
     ServeState *st = h->serve;
@@ -537,7 +540,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
             wd.a0 = sch.a0;
             wd.s_end = sch.s_end;
             it.cost = (double)sch.s_end * kVariants[it.variant][0];
-            it.cap = ring_need(wd, kVariants[it.variant][0]);
+            it.cap = ring_need(wd, kVariants[it.variant][0], h->plan.ring_bin_shift);
             items.push_back(it);
             read_of.push_back((int)chunk_idx);
             // the band of this piece's last row is the row above the next piece
@@ -579,9 +582,6 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         delete f;
         return RA_EINVAL;
     }
-    std::vector<WorkDesc> work(n_items);
-    for (uint32_t x = 0; x < n_items; ++x)
-        work[x] = items[order[x]].wd;
     // device memory for this flush
     auto take = [&](uint64_t bytes) -> void * {
         void *p = h->arena.alloc(std::max<uint64_t>(bytes, 256));
@@ -589,21 +589,20 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
             f->blocks.push_back(p);
         return p;
     };
-    float *d_ev = (float *)take(sizeof(float) * ev.size());
-    SigDesc *d_sig = (SigDesc *)take(sizeof(SigDesc) * sig.size());
-    WorkDesc *d_work = (WorkDesc *)take(sizeof(WorkDesc) * n_items);
-    f->d_res = (rawalign_result_t *)take(sizeof(rawalign_result_t) * n_items);
-    unsigned long long *d_keys = (unsigned long long *)take(sizeof(unsigned long long) * chunk_idx);
-    int *d_read_of = (int *)take(sizeof(int) * n_items);
-    int *d_queue = (int *)take(sizeof(int) * (kMaxClasses + 2));
-    bool ok = d_ev && d_sig && d_work && f->d_res && d_keys && d_read_of && d_queue;
-    if (ok)
-        ok = finalize_classes(h->sm_count, classes, take) == RA_OK;
-    // pinned staging: inputs in one buffer, results in another
+    // the flush's inputs live in one arena block and travel in one copy:
+    // events, signal descriptors, work records, read slots, and the zeroed
+    // per-chunk best keys and queue counters
+    auto al256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t b_ev = sizeof(float) * ev.size(), b_sig = sizeof(SigDesc) * sig.size();
     const size_t b_work = sizeof(WorkDesc) * n_items, b_rd = sizeof(int) * n_items;
-    const size_t o_sig = (b_ev + 255) & ~255ull, o_work = o_sig + ((b_sig + 255) & ~255ull);
-    const size_t o_rd = o_work + ((b_work + 255) & ~255ull), in_bytes = o_rd + b_rd + 256;
+    const size_t b_keys = sizeof(unsigned long long) * chunk_idx, b_q = sizeof(int) * (kMaxClasses + 2);
+    const size_t o_sig = al256(b_ev), o_work = o_sig + al256(b_sig), o_rd = o_work + al256(b_work);
+    const size_t o_keys = o_rd + al256(b_rd), o_q = o_keys + al256(b_keys), in_bytes = o_q + al256(b_q);
+    char *d_in = (char *)take(in_bytes);
+    f->d_res = (rawalign_result_t *)take(sizeof(rawalign_result_t) * n_items);
+    bool ok = d_in && f->d_res;
+    if (ok)
+        ok = finalize_classes(h->sm_count, classes, take) == RA_OK;
     if (ok) {
         f->h_in = st->pinned.get(in_bytes);
         f->h_res = (rawalign_result_t *)st->pinned.get(sizeof(rawalign_result_t) * std::max<uint32_t>(n_items, 1));
@@ -618,11 +617,20 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         delete f;
         return RA_ENOMEM;
     }
+    float *d_ev = (float *)d_in;
+    SigDesc *d_sig = (SigDesc *)(d_in + o_sig);
+    WorkDesc *d_work = (WorkDesc *)(d_in + o_work);
+    int *d_read_of = (int *)(d_in + o_rd);
+    unsigned long long *d_keys = (unsigned long long *)(d_in + o_keys);
+    int *d_queue = (int *)(d_in + o_q);
     char *hin = (char *)f->h_in;
     memcpy(hin, ev.data(), b_ev);
     memcpy(hin + o_sig, sig.data(), b_sig);
-    memcpy(hin + o_work, work.data(), b_work);
+    WorkDesc *hw = (WorkDesc *)(hin + o_work);
+    for (uint32_t x = 0; x < n_items; ++x)
+        hw[x] = items[order[x]].wd;
     memcpy(hin + o_rd, read_of.data(), b_rd);
+    memset(hin + o_keys, 0, in_bytes - o_keys);
     cudaStream_t s = h->stream;
     // timing events (start, inputs copied, kernels done, done), reused
     while (st->timing_events.size() < 4) {
@@ -637,13 +645,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     f->done = st->timing_events.back();
     st->timing_events.pop_back();
     RA_CUDA(cudaEventRecord(f->t_ev[0], s));
-    RA_CUDA(cudaMemcpyAsync(d_ev, hin, b_ev, cudaMemcpyHostToDevice, s));
-    if (!sig.empty())
-        RA_CUDA(cudaMemcpyAsync(d_sig, hin + o_sig, b_sig, cudaMemcpyHostToDevice, s));
-    RA_CUDA(cudaMemcpyAsync(d_work, hin + o_work, b_work, cudaMemcpyHostToDevice, s));
-    RA_CUDA(cudaMemcpyAsync(d_read_of, hin + o_rd, b_rd, cudaMemcpyHostToDevice, s));
-    RA_CUDA(cudaMemsetAsync(d_keys, 0, sizeof(unsigned long long) * chunk_idx, s));
-    RA_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int) * (kMaxClasses + 2), s));
+    RA_CUDA(cudaMemcpyAsync(d_in, hin, in_bytes, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaEventRecord(f->t_ev[1], s));
     float *abase = (float *)h->arena.base;
     if (!sig.empty())
@@ -707,6 +709,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
 extern "C" int rawalign_dtw_poll_chunks(rawalign_dtw_t *h, const uint64_t *tickets, uint32_t n_tickets,
                                         rawalign_result_t *out, uint32_t cap, uint32_t *counts, int64_t timeout_us)
 {
+    NvtxRange nvtx_range("rawalign_dtw_poll_chunks");
     if (!h || (n_tickets && (!tickets || !counts)) || (cap && !out))
         return RA_EINVAL;
     ServeState *st = h->serve;

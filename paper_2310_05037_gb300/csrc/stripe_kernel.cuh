@@ -6,9 +6,11 @@
 // global queue when it finishes).  Rows (read events) are cut into stripes of
 // H = G*HR rows; lane t of stripe k owns rows i0..i0+HR-1 (i0 = k*H + t*HR)
 // and keeps their events and previous-column DP values in registers.  Each
-// step a lane computes one column j for its HR rows; lane t runs one column
-// behind lane t-1 and receives D(i0-1, j) from lane t-1's bottom row by
-// __shfl_up_sync.  A lane does not wait for the stripe to finish: once it has
+// step a lane computes one column j for its HR rows; lane t runs kLaneLag = 2
+// columns behind lane t-1 and receives D(i0-1, j) from lane t-1's bottom row
+// of two steps back by __shfl_up_sync, so that a lane's next two columns
+// depend on nothing its neighbour computes meanwhile and can be computed as
+// two interleaved dependency chains.  A lane does not wait for the stripe to finish: once it has
 // passed the last in-band column of its rows it takes the same rows of the
 // next stripe, dC steps later in its own schedule.  The first lane of a
 // stripe reads its row above from a ring buffer that the last lane of the
@@ -102,7 +104,8 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
     int loA = kBigCol;
     unsigned widA = 0;
     bool writer = false, holds_last = false;
-    float diag = kInf, bottom = kInf, rnext = kInf, rjn = 0.f;
+    float diag = kInf, rnext = kInf, rnext2 = kInf, rjn = 0.f, rjn2 = 0.f;
+    float b1 = kInf, b2 = kInf;  // this lane's bottom row one and two steps back
     float best = kInf;
     int bestj = -1;
     int lastLo = kBigCol, r_last = 0;
@@ -184,6 +187,223 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         holds_last = false;
         nvalid = 0;
         colmax = -1;
+    };
+
+    // rows [loN, hiN) of the lane are in band at the current column: one
+    // bit-field mask instruction (and the in-band cells of the step)
+    auto band_mask = [&]() -> unsigned {
+        const int Aq = Bq - Dq - (Br < Dr ? 1 : 0);
+        const int loN = max(Aq, 0);
+        const int hiN = min(Bq + 1, nvalid);
+        const int width = max(hiN - loN, 0);
+        unsigned M;
+        asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(M) : "r"(loN), "r"(width));
+        M = ((unsigned)j <= (unsigned)colmax) ? M : 0u;
+        ncells += __popc(M);
+        return M;
+    };
+    auto dda_step = [&]() {
+        Bq += cq;
+        Br += cr;
+        if (Br >= cnum) {
+            Bq += 1;
+            Br -= cnum;
+        }
+    };
+    auto last_row_value = [&](float v, int col) {
+        // FREE end: running minimum of the last row (smallest column on
+        // ties) and the frontier row kept for the next chunk (serving)
+        if (v < best) {
+            best = v;
+            bestj = col;
+        }
+        if (p.fstore_out && (unsigned)(col - lastLo) <= lastWid)
+            p.fstore_out[gc->fout_off + (unsigned)(col - gc->fout_lo)] = v;
+    };
+    auto wrap_if_needed = [&]() {
+        if (j > b) {
+            // this lane leaves stripe k
+            if (holds_last) {
+                float v = kInf;
+                const int rl = gc->r_last;
+#pragma unroll
+                for (int r = 0; r < HR; ++r)
+                    if (r == rl)
+                        v = D[r];
+                const int row_last = gc->row0 + gc->nrows - 1;
+                float cost;
+                int ei, ej;
+                if (FREE_END) {
+                    cost = best;
+                    ej = bestj;
+                    ei = bestj >= 0 ? row_last : -1;
+                } else {
+                    cost = (b == m - 1) ? v : kInf;
+                    ei = row_last;
+                    ej = m - 1;
+                }
+                const int cand = gc->cand, read = gc->read;
+                const float sc = __fsub_rn(__fmul_rn(p.b_match, (float)gc->n_read), cost);
+                rawalign_result_t *o = p.results + cand;
+                o->read_id = (uint64_t)read;
+                o->cand_idx = (uint32_t)cand;
+                o->cost = cost;
+                o->score = sc;
+                o->end_i = ei;
+                o->end_j = ej;
+                o->w_eff = gc->w_rep;
+                o->status = 0;
+                atomicMax(p.best_keys + read, best_key(sc, cand));
+                if (ET)
+                    gc->written = 1;
+            }
+            if (ET && writer) {
+                // branch and bound (Sec. 2.4.1): every path crosses the
+                // stripe's last row and cells only add, so the final cost
+                // is at least that row's smallest value; stop when even
+                // that bound cannot beat the read's best score so far
+                const unsigned long long key =
+                    *(volatile const unsigned long long *)(p.best_keys + gc->read);
+                const float best = key ? key_score(key) : -kInf;
+                const float ub = __fsub_rn(__fmul_rn(p.b_match, (float)gc->n_read), rowmin);
+                if (ub < best) {
+                    gc->lb = rowmin;
+                    gc->abort = 1;
+                }
+            }
+            ++k;
+            if (k < gc->K) {
+                const int den = gc->den, qH = gc->qH, rH = gc->rH;
+                int Q = lc->loQ + qH, R = lc->loR + rH;
+                if (R >= den) {
+                    Q += 1;
+                    R -= den;
+                }
+                lc->loQ = Q;
+                lc->loR = R;
+                Q = lc->hiQ + qH;
+                R = lc->hiR + rH;
+                if (R >= den) {
+                    Q += 1;
+                    R -= den;
+                }
+                lc->hiQ = Q;
+                lc->hiR = R;
+                setup_stripe();
+                j -= gc->dC;
+                {
+                    const int qdC = gc->qdC, rdC = gc->rdC;
+                    Bq -= H + qdC;
+                    Br -= rdC;
+                    if (Br < 0) {
+                        Bq -= 1;
+                        Br += cnum;
+                    }
+                }
+            } else {
+                finish_lane();
+            }
+            // the lane's columns jumped: fetch the current and the next
+            rnext = ring[j & rmask];
+            rnext2 = ring[(j + 1) & rmask];
+            rjn = __ldg(rr + min((unsigned)j, (unsigned)(m - 1)));
+            rjn2 = __ldg(rr + min((unsigned)(j + 1), (unsigned)(m - 1)));
+        }
+    };
+    // one column of the lane's rows
+    auto single_step = [&](bool check) {
+        ++j;
+        dda_step();
+        if (check)
+            wrap_if_needed();
+        const float rc = rnext;
+        rnext = rnext2;
+        rnext2 = ring[(j + 2) & rmask];
+        const float sh = __shfl_up_sync(FULL, b2, 1, G);
+        const float src = (t == 0) ? rc : sh;
+        const float upv = ((unsigned)(j - loA) <= widA) ? src : kInf;
+        const float rj = rjn;
+        rjn = rjn2;
+        rjn2 = __ldg(rr + min((unsigned)(j + 2), (unsigned)(m - 1)));
+        const unsigned M = band_mask();
+        float nn = upv, nw = diag, fv = kInf;
+#pragma unroll
+        for (int r = 0; r < HR; ++r) {
+            const float eg = ((M >> r) & 1u) ? e[r] : kInf;
+            const float v = __fadd_rn(fabsf(__fsub_rn(eg, rj)), min3f(nw, nn, D[r]));
+            nw = D[r];
+            D[r] = v;
+            nn = v;
+            if (FREE_END && r == r_last)
+                fv = v;
+        }
+        diag = upv;
+        const float bottom = D[HR - 1];
+        b2 = b1;
+        b1 = bottom;
+        if (ET)
+            rowmin = fminf(rowmin, bottom);
+        if (FREE_END && holds_last)
+            last_row_value(fv, j);
+        if (RING_SMEM)
+            st_shared_if(writer, ring + (j & rmask), bottom);
+        else if (writer)
+            ring[j & rmask] = bottom;
+        __syncwarp();
+    };
+    // two columns of the lane's rows, as two interleaved chains
+    auto pair_step = [&]() {
+        ++j;
+        dda_step();
+        const int jA = j;
+        const unsigned MA = band_mask();
+        ++j;
+        dda_step();
+        const unsigned MB = band_mask();
+        const float rcA = rnext, rcB = rnext2;
+        rnext = ring[(j + 1) & rmask];
+        rnext2 = ring[(j + 2) & rmask];
+        const float shA = __shfl_up_sync(FULL, b2, 1, G);
+        const float shB = __shfl_up_sync(FULL, b1, 1, G);
+        const float upvA = ((unsigned)(jA - loA) <= widA) ? ((t == 0) ? rcA : shA) : kInf;
+        const float upvB = ((unsigned)(j - loA) <= widA) ? ((t == 0) ? rcB : shB) : kInf;
+        const float rjA = rjn, rjB = rjn2;
+        rjn = __ldg(rr + min((unsigned)(j + 1), (unsigned)(m - 1)));
+        rjn2 = __ldg(rr + min((unsigned)(j + 2), (unsigned)(m - 1)));
+        float nnA = upvA, nwA = diag, nnB = upvB, nwB = upvA, fvA = kInf, fvB = kInf;
+#pragma unroll
+        for (int r = 0; r < HR; ++r) {
+            const float egA = ((MA >> r) & 1u) ? e[r] : kInf;
+            const float egB = ((MB >> r) & 1u) ? e[r] : kInf;
+            const float vA = __fadd_rn(fabsf(__fsub_rn(egA, rjA)), min3f(nwA, nnA, D[r]));
+            nwA = D[r];
+            nnA = vA;
+            const float vB = __fadd_rn(fabsf(__fsub_rn(egB, rjB)), min3f(nwB, nnB, vA));
+            nwB = vA;
+            nnB = vB;
+            D[r] = vB;
+            if (FREE_END && r == r_last) {
+                fvA = vA;
+                fvB = vB;
+            }
+        }
+        diag = upvB;
+        b2 = nnA;
+        b1 = nnB;
+        if (ET)
+            rowmin = fminf(rowmin, fminf(nnA, nnB));
+        if (FREE_END && holds_last) {
+            last_row_value(fvA, jA);
+            last_row_value(fvB, j);
+        }
+        if (RING_SMEM) {
+            st_shared_if(writer, ring + (jA & rmask), nnA);
+            st_shared_if(writer, ring + (j & rmask), nnB);
+        } else if (writer) {
+            ring[jA & rmask] = nnA;
+            ring[j & rmask] = nnB;
+        }
+        __syncwarp();
     };
 
     lc->cells = 0;
@@ -273,7 +493,9 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                         best = kInf;
                         bestj = -1;
                         k = 0;
-                        j = wd.a0 - 1 - t;  // first column of this lane
+                        j = wd.a0 - 1 - kLaneLag * t;  // first column of this lane
+                        b1 = kInf;
+                        b2 = kInf;
                         {
                             int Aq, Ar;
                             if (num == 0) {
@@ -344,11 +566,9 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                 break;
             __syncwarp();
             rnext = ring[(j + 1) & rmask];
-            {
-                int jc = j + 1 < 0 ? 0 : j + 1;
-                jc = jc > m - 1 ? m - 1 : jc;
-                rjn = __ldg(rr + jc);
-            }
+            rnext2 = ring[(j + 2) & rmask];
+            rjn = __ldg(rr + min((unsigned)(j + 1), (unsigned)(m - 1)));
+            rjn2 = __ldg(rr + min((unsigned)(j + 2), (unsigned)(m - 1)));
             continue;
         }
 
@@ -358,161 +578,25 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         // abort flag; otherwise at most 2^27 steps, so that the lane's cell
         // count, at most HR < 32 per step, fits in 32 bits until it is flushed)
         const int nstep = __reduce_min_sync(FULL, ET ? min(rem, 64) : min(rem, 1 << 27));
-#pragma unroll 2
-        for (int q = 0; q < nstep; ++q) {
-            ++j;
-            {
-                Bq += cq;
-                Br += cr;
-                if (Br >= cnum) {
-                    Bq += 1;
-                    Br -= cnum;
-                }
+        // Runs of steps in which no lane of the warp changes stripe go two
+        // columns at a time: the two columns are computed as two interleaved
+        // chains (column j+1's row r needs column j's rows r-1 and r, and
+        // the row above from the neighbour lane's bottom kLaneLag = 2 steps
+        // back), so the schedulers see two independent dependency chains.
+        // A step in which some lane changes stripe runs alone.
+        int q = 0;
+        while (q < nstep) {
+            const int mine = (b == INT_MAX) ? INT_MAX : max(b - j, 0);
+            const int run = __reduce_min_sync(FULL, min(mine, nstep - q));
+            for (int x = 0; x + 1 < run; x += 2)
+                pair_step();
+            if (run & 1)
+                single_step(false);
+            q += run;
+            if (q < nstep) {
+                single_step(true);
+                ++q;
             }
-            if (j > b) {
-                // this lane leaves stripe k
-                if (holds_last) {
-                    float v = kInf;
-                    const int rl = gc->r_last;
-#pragma unroll
-                    for (int r = 0; r < HR; ++r)
-                        if (r == rl)
-                            v = D[r];
-                    const int row_last = gc->row0 + gc->nrows - 1;
-                    float cost;
-                    int ei, ej;
-                    if (FREE_END) {
-                        cost = best;
-                        ej = bestj;
-                        ei = bestj >= 0 ? row_last : -1;
-                    } else {
-                        cost = (b == m - 1) ? v : kInf;
-                        ei = row_last;
-                        ej = m - 1;
-                    }
-                    const int cand = gc->cand, read = gc->read;
-                    const float sc = __fsub_rn(__fmul_rn(p.b_match, (float)gc->n_read), cost);
-                    rawalign_result_t *o = p.results + cand;
-                    o->read_id = (uint64_t)read;
-                    o->cand_idx = (uint32_t)cand;
-                    o->cost = cost;
-                    o->score = sc;
-                    o->end_i = ei;
-                    o->end_j = ej;
-                    o->w_eff = gc->w_rep;
-                    o->status = 0;
-                    atomicMax(p.best_keys + read, best_key(sc, cand));
-                    if (ET)
-                        gc->written = 1;
-                }
-                if (ET && writer) {
-                    // branch and bound (Sec. 2.4.1): every path crosses the
-                    // stripe's last row and cells only add, so the final cost
-                    // is at least that row's smallest value; stop when even
-                    // that bound cannot beat the read's best score so far
-                    const unsigned long long key =
-                        *(volatile const unsigned long long *)(p.best_keys + gc->read);
-                    const float best = key ? key_score(key) : -kInf;
-                    const float ub = __fsub_rn(__fmul_rn(p.b_match, (float)gc->n_read), rowmin);
-                    if (ub < best) {
-                        gc->lb = rowmin;
-                        gc->abort = 1;
-                    }
-                }
-                ++k;
-                if (k < gc->K) {
-                    const int den = gc->den, qH = gc->qH, rH = gc->rH;
-                    int Q = lc->loQ + qH, R = lc->loR + rH;
-                    if (R >= den) {
-                        Q += 1;
-                        R -= den;
-                    }
-                    lc->loQ = Q;
-                    lc->loR = R;
-                    Q = lc->hiQ + qH;
-                    R = lc->hiR + rH;
-                    if (R >= den) {
-                        Q += 1;
-                        R -= den;
-                    }
-                    lc->hiQ = Q;
-                    lc->hiR = R;
-                    setup_stripe();
-                    j -= gc->dC;
-                    {
-                        const int qdC = gc->qdC, rdC = gc->rdC;
-                        Bq -= H + qdC;
-                        Br -= rdC;
-                        if (Br < 0) {
-                            Bq -= 1;
-                            Br += cnum;
-                        }
-                    }
-                } else {
-                    finish_lane();
-                }
-                rnext = ring[j & rmask];
-                int jc = j < 0 ? 0 : j;
-                jc = jc > m - 1 ? m - 1 : jc;
-                rjn = __ldg(rr + jc);
-            }
-
-            const float rc = rnext;
-            rnext = ring[(j + 1) & rmask];
-            const float sh = __shfl_up_sync(FULL, bottom, 1, G);
-            const float src = (t == 0) ? rc : sh;
-            const float upv = ((unsigned)(j - loA) <= widA) ? src : kInf;
-            const float rj = rjn;
-            {
-                int jc = j + 1 < 0 ? 0 : j + 1;
-                jc = jc > m - 1 ? m - 1 : jc;
-                rjn = __ldg(rr + jc);
-            }
-            float eg[HR];
-            {
-                // rows [loN, hiN) are in band: one bit-field mask instruction
-                const int Aq = Bq - Dq - (Br < Dr ? 1 : 0);
-                const int loN = max(Aq, 0);
-                const int hiN = min(Bq + 1, nvalid);
-                const int width = max(hiN - loN, 0);
-                unsigned M;
-                asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(M) : "r"(loN), "r"(width));
-                M = ((unsigned)j <= (unsigned)colmax) ? M : 0u;
-                ncells += __popc(M);
-#pragma unroll
-                for (int r = 0; r < HR; ++r)
-                    eg[r] = ((M >> r) & 1u) ? e[r] : kInf;
-            }
-            float nn = upv, nw = diag;
-#pragma unroll
-            for (int r = 0; r < HR; ++r) {
-                const float v = __fadd_rn(fabsf(__fsub_rn(eg[r], rj)), min3f(nw, nn, D[r]));
-                nw = D[r];
-                D[r] = v;
-                nn = v;
-            }
-            diag = upv;
-            bottom = D[HR - 1];
-            if (ET)
-                rowmin = fminf(rowmin, bottom);
-            if (FREE_END && holds_last) {
-                float fv = kInf;
-#pragma unroll
-                for (int r = 0; r < HR; ++r)
-                    if (r == r_last)
-                        fv = D[r];
-                if (fv < best) {
-                    best = fv;
-                    bestj = j;
-                }
-                if (p.fstore_out && (unsigned)(j - lastLo) <= lastWid)
-                    p.fstore_out[gc->fout_off + (unsigned)(j - gc->fout_lo)] = fv;
-            }
-            if (RING_SMEM)
-                st_shared_if(writer, ring + (j & rmask), bottom);
-            else if (writer)
-                ring[j & rmask] = bottom;
-            __syncwarp();
         }
         s += nstep;
         lc->cells += ncells;

@@ -134,6 +134,7 @@ extern "C" int rawalign_dtw_traceback(rawalign_dtw_t *h, const float *events, ui
                                       const rawalign_candidate_t *cand, int32_t end_mode, int32_t *path_i,
                                       int32_t *path_j, uint32_t cap, uint32_t *path_len, rawalign_result_t *result)
 {
+    NvtxRange nvtx_range("rawalign_dtw_traceback");
     if (!h || !events || !cand || !path_i || !path_j || !path_len || !result || n_events == 0)
         return RA_EINVAL;
     if (end_mode != RA_END_GLOBAL && end_mode != RA_END_FREE)

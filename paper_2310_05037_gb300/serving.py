@@ -149,6 +149,7 @@ class ServingLoop:
             closes = np.array(to_close, np.int64)
             to_close = []
             if len(q) or len(closes):
+                t_start = time.perf_counter()  # a chunk's latency runs from here to its result on the host
                 ch = np.concatenate([self._chunks(q, pos[q], False), self._chunks(closes, pos[closes], True)])
                 a = time.perf_counter()
                 tickets, status = B.rawalign_dtw_submit_chunks(h, ch, self.events, self.cands)
@@ -169,7 +170,7 @@ class ServingLoop:
                 B.rawalign_dtw_flush(h)
                 t_flush += time.perf_counter() - a
                 st.flushes += 1
-                gens.append((tickets[: len(q)][ok], qs, time.perf_counter(), tickets[len(q):]))
+                gens.append((tickets[: len(q)][ok], qs, t_start, tickets[len(q):]))
             # read back the oldest generation: in closed loop when the others
             # are on the GPU (or nothing else can start), in real time as soon
             # as it has completed
@@ -253,50 +254,49 @@ class Trajectory:
 
 
 def collect_trajectories(aligner, reads, chunk=180, max_events=4000, in_flight=512):
-    """Feeds every read chunk by chunk up to max_events (or its end) through
-    submit_chunk / flush / poll, keeping in_flight reads admitted, and
-    records each read's trajectory.  Reads are not stopped early, so every
-    threshold can be studied on the same trajectories."""
-    pending = list(reads)
-    live = {}
-    out = {}
-    while pending or live:
-        while pending and len(live) < in_flight:
-            rd = pending[0]
-            q = min(chunk, len(rd.events), max_events)
-            last = q >= min(max_events, len(rd.events))
-            try:
-                t = B.rawalign_dtw_submit_chunk(aligner.h, rd.read_id, rd.events[:q], rd.cands, last)
-            except B.RawAlignError as e:
-                if e.code == B.RA_EAGAIN:
-                    break
-                raise
-            pending.pop(0)
-            live[rd.read_id] = [rd, q, t]
-            out[rd.read_id] = Trajectory(rd.read_id, rd.on_target, getattr(rd, "true_cand", -1))
-        B.rawalign_dtw_flush(aligner.h)
-        done = []
-        for rid, st in live.items():
-            rd, q, t = st
-            res = B.rawalign_dtw_poll(aligner.h, t, 64, timeout_us=-1)
-            tr = out[rid]
-            sc = res["score"].astype(np.float64)
+    """Feeds every read chunk by chunk up to max_events (or its end) and
+    records each read's trajectory.  Up to in_flight reads are admitted at a
+    time and advance together: one submit_chunks, one flush and one
+    poll_chunks per round.  Reads are not stopped early, so every threshold
+    can be studied on the same trajectories."""
+    loop = ServingLoop(aligner, reads, chunk=chunk, max_events=max_events)
+    h = aligner.h
+    n = len(loop.reads)
+    out = [Trajectory(rd.read_id, rd.on_target, getattr(rd, "true_cand", -1)) for rd in loop.reads]
+    pos = np.zeros(n, np.int64)
+    todo = list(range(n))
+    live = []
+    while todo or live:
+        while todo and len(live) < in_flight:
+            live.append(todo.pop(0))
+        q = np.array(live, np.int64)
+        ch = loop._chunks(q, pos[q], False)
+        tickets, status = B.rawalign_dtw_submit_chunks(h, ch, loop.events, loop.cands)
+        if np.any((status != B.RA_OK) & (status != B.RA_EAGAIN)):
+            raise B.RawAlignError("rawalign_dtw_submit_chunks", int(status[status != B.RA_OK][0]))
+        ok = status == B.RA_OK
+        if not ok.any():
+            raise RuntimeError("no read admitted: too few serving slots or too little arena memory")
+        B.rawalign_dtw_flush(h)
+        res, counts = B.rawalign_dtw_poll_chunks(h, tickets[ok], int(loop.n_cand[q[ok]].sum()))
+        at = 0
+        qs = q[ok]
+        pos[qs] += ch["n_events"][ok].astype(np.int64)
+        for x, k in zip(qs.tolist(), counts.tolist()):
+            r = res[at:at + k]
+            at += k
+            tr = out[x]
+            sc = r["score"].astype(np.float64)
             b = int(np.argmax(sc)) if len(sc) else -1
-            tr.events.append(q)
+            tr.events.append(int(pos[x]))
             tr.best_score.append(float(sc[b]) if b >= 0 else -np.inf)
             tr.best_cand.append(b)
-            tr.min_cost.append(float(res["cost"].min()) if len(res) else np.inf)
-            tr.mapped.append(bool(len(res) and np.any(res["decision"] == B.RA_MAPPED)))
-            end = min(max_events, len(rd.events))
-            if q >= end:
-                done.append(rid)
-                continue
-            q2 = min(q + chunk, end)
-            st[1] = q2
-            st[2] = B.rawalign_dtw_submit_chunk(aligner.h, rid, rd.events[q:q2], None, q2 >= end)
-        for rid in done:
-            live.pop(rid)
-    return [out[rd.read_id] for rd in reads if rd.read_id in out]
+            tr.min_cost.append(float(r["cost"].min()) if len(r) else np.inf)
+            tr.mapped.append(bool(len(r) and np.any(r["decision"] == B.RA_MAPPED)))
+        # finished reads leave; refused ones stay and retry their first chunk
+        done = set(qs[pos[qs] >= loop.n_ev[qs]].tolist())
+        live = [x for x in live if x not in done]
+    return out
 
 
 def decision_study(trajectories, thresholds, b_match=0.4, max_events=4000):

@@ -460,36 +460,82 @@ class ServingRead:
 
 def config_serving(seed: int = 0x5EED0004, n_reads: int = 2048, ref_len: int = 100_000_000,
                    max_events: int = 4000, cmax: int = 32, band: int = 64, off_target: float = 0.5,
-                   rate_per_s: float = 1280.0):
+                   rate_per_s: float = 1280.0, noise_sd: float = 0.3, dup_frac: float = 0.0,
+                   block: int = 5000, ident: float = 0.90, repeat_reads: float = 0.0):
     """Serving loop inputs: reads that arrive as a Poisson stream (mean rate
     chosen so that about 512 are in flight at 0.4 s per 180-event chunk),
     <= 4000 events each, up to 32 candidates (1 true when on-target), band 64.
     Each candidate carries the band slope the sequencer model implies:
     1 / (0.95 * 1.1) = 1000/1045 reference values per event (mean dwell 1.1
-    events per k-mer, 5 % skipped k-mers).  Returns
-    (pore, ref2bit, ref_len, [ServingRead])."""
+    events per k-mer, 5 % skipped k-mers).
+
+    With dup_frac > 0 the reference has that share of its `block`-base blocks
+    overwritten by copies of other blocks at `ident` identity (as the
+    Read-Until prefix workload) and about half of the decoys sit in copied
+    blocks.  With repeat_reads > 0 that share of the reads come from a block
+    that has a copy, and the copy's matching region is one of the decoys: for
+    an on-target read a near-duplicate of its true locus, for an off-target
+    read a near-duplicate of where its signal came from (the cases where the
+    decision can go wrong).  Returns (pore, ref2bit, ref_len, [ServingRead])."""
     rng = np.random.Generator(np.random.PCG64(seed))
     pore = pore_table(seed ^ 0xA5A5)
     ref = hashed_reference(seed, ref_len)
+    span = int(math.ceil(max_events * 1000 / 1045)) + 2 * band + K
+    pairs = []
+    if dup_frac > 0:
+        n_blocks = ref_len // block
+        n_dup = max(1, int(dup_frac * n_blocks))
+        dst = rng.choice(n_blocks, size=n_dup, replace=False)
+        srcs = rng.integers(0, n_blocks, size=n_dup)
+        for d, sb in zip(dst.tolist(), srcs.tolist()):
+            if d == sb:
+                continue
+            codes = unpack_bases(ref, sb * block, block).copy()
+            mut = rng.random(block) < (1.0 - ident)
+            codes[mut] = (codes[mut] + rng.integers(1, 4, size=int(mut.sum()))).astype(np.uint8) & 3
+            write_bases_fast(ref, d * block, codes)
+            pairs.append((sb, d))
+    # a read from a copied block walks 2 * max_events + K bases from its start
+    walk_len = 2 * max_events + K
+    fits = block - max(span, walk_len)
     out = []
     t = 0.0
-    span = int(math.ceil(max_events * 1000 / 1045)) + 2 * band + K
     for q in range(n_reads):
         t += rng.exponential(1.0 / rate_per_s)
-        loc = int(rng.integers(0, ref_len - 3 * max_events - span))
-        walk = unpack_bases(ref, loc, 2 * max_events + K)
-        ev = simulate_events(rng, walk, pore, max_events, 0.3, 0.05)
+        rep = None
+        if pairs and fits > 0 and rng.random() < repeat_reads:
+            sb, d = pairs[int(rng.integers(0, len(pairs)))]
+            o = int(rng.integers(0, fits))
+            rep = (sb * block + o, d * block + o)
+        loc = rep[0] if rep else int(rng.integers(0, ref_len - 3 * max_events - span))
+        walk = unpack_bases(ref, loc, walk_len)
+        ev = simulate_events(rng, walk, pore, max_events, noise_sd, 0.05)
         on = bool(rng.random() >= off_target)
         if not on:  # events from somewhere else than every candidate
             loc2 = int(rng.integers(0, ref_len - 3 * max_events - span))
-            walk = unpack_bases(ref, loc2, 2 * max_events + K)
-            ev = simulate_events(rng, walk, pore, max_events, 0.3, 0.05)
+            walk = unpack_bases(ref, loc2, walk_len)
+            ev_off = simulate_events(rng, walk, pore, max_events, noise_sd, 0.05)
+            if rep is None:
+                ev = ev_off
+            # else: the signal stays that of the copied block's source, which is
+            # not a candidate; its near-duplicate (the copy) is
         nc = int(rng.integers(1, cmax + 1))
+        if rep and nc < 2:
+            nc = 2
         c = np.zeros(nc, CANDIDATE_DTYPE)
         true_slot = int(rng.integers(0, nc))
-        for s in range(nc):
-            off = loc if (on and s == true_slot) else int(rng.integers(0, ref_len - span))
-            c[s] = (q, off, span, 0, 0, band, 0, 1000, 1045)
+        copy_slot = (true_slot + 1 + int(rng.integers(0, nc - 1))) % nc if rep else -1
+        for s_ in range(nc):
+            if on and s_ == true_slot:
+                off = loc
+            elif s_ == copy_slot:
+                off = rep[1]
+            elif pairs and dup_frac > 0 and rng.random() < 0.5:
+                d = pairs[int(rng.integers(0, len(pairs)))][1]
+                off = min(d * block + int(rng.integers(0, max(1, block - span))), ref_len - span)
+            else:
+                off = int(rng.integers(0, ref_len - span))
+            c[s_] = (q, off, span, 0, 0, band, 0, 1000, 1045)
         out.append(ServingRead(q, ev, c, on, t, true_cand=true_slot if on else -1))
     return pore, ref, ref_len, out
 

@@ -6,7 +6,11 @@
 //     in-band column of its rows (its first step there is fully out of band);
 //   - every value lane 0 takes from the ring (the row above its stripe, in
 //     band) is the one the last lane of the previous stripe wrote, with the
-//     ring size ring_need() gives and the kernel's read-before-write order;
+//     ring size ring_need() gives, lanes kLag columns apart, and the kernel's
+//     timing taken at its loosest: a write is seen only two steps later (two
+//     columns go together, one warp barrier per pair), a read may happen two
+//     steps before the value is used (two-deep prefetch), and nothing may
+//     overwrite the entry between the write and the use;
 //   - the lane holding the last row leaves it within s_end steps.
 // It also checks make_classes: classes are runs of one variant and ring
 // size, longest first inside a class (first candidates before the others),
@@ -56,19 +60,25 @@ static void check_schedule(const BandDef &band, int64_t n, int G, int HR, uint64
         b[t] = (r0 > n - 1) ? -1 : band.hi(r1);
     };
     for (int t = 0; t < G; ++t) {
-        j[t] = sc.a0 - 2 - t;  // the first step computes column a0 - 1 - t
+        j[t] = sc.a0 - 2 - (int64_t)kLag * t;  // the first step computes column a0 - 1 - kLag t
         set_b(t);
         int64_t r0, r1;
         lane_rows(0, t, r0, r1);
         if (r0 <= n - 1)
             CHECK(j[t] + 1 < band.lo(r0), "start not out of band: G%d HR%d t%d\n", G, HR, t);
     }
-    std::vector<std::pair<int64_t, int64_t>> tag(cap, {-9, 0});  // (stripe, column) last written
-    std::pair<int64_t, int64_t> prefetched{-9, 0};
+    // per ring slot: every write as (step, stripe, column)
+    struct Wr {
+        int64_t step, stripe, col;
+    };
+    std::vector<std::vector<Wr>> writes(cap);
+    struct Use {
+        int64_t step, stripe, col;
+    };
+    std::vector<Use> uses;
     const int t_last = (int)((n - 1 - (K - 1) * H) / HR);
     int64_t holder_done = -1;
     for (int64_t s = 0; s < sc.s_end; ++s) {
-        bool moved0 = false;
         for (int t = 0; t < G; ++t) {
             ++j[t];
             if (j[t] > b[t]) {
@@ -86,26 +96,33 @@ static void check_schedule(const BandDef &band, int64_t n, int G, int HR, uint64
                 } else {
                     b[t] = INT64_MAX;
                 }
-                if (t == 0)
-                    moved0 = true;
             }
         }
-        // lane 0's value for its column: re-read this step after a stripe
-        // change, else prefetched last step (both before this step's store)
-        const std::pair<int64_t, int64_t> got = moved0 ? tag[j[0] & mask] : prefetched;
         if (k[0] >= 1 && k[0] < K) {
             const int64_t above = k[0] * H - 1, c = j[0];
             if (c >= band.lo(above) && c <= band.hi(above))
-                CHECK(got.first == k[0] - 1 && got.second == c,
-                      "ring: G%d HR%d n%lld stripe %lld column %lld got (%lld,%lld) cap %lld dC %lld\n", G, HR,
-                      (long long)n, (long long)k[0], (long long)c, (long long)got.first, (long long)got.second,
-                      (long long)cap, (long long)dC);
+                uses.push_back({s, k[0], c});
         }
-        prefetched = tag[(j[0] + 1) & mask];
         const int w = G - 1;
         if (k[w] < K - 1)
-            tag[j[w] & mask] = {k[w], j[w]};
+            writes[j[w] & mask].push_back({s, k[w], j[w]});
         ++steps_checked;
+    }
+    for (const Use &u : uses) {
+        // the entry must hold (stripe - 1, column) from two steps before the
+        // earliest read (use - 2) to the use, written by nothing else meanwhile
+        const auto &ws = writes[u.col & mask];
+        const Wr *last = nullptr;
+        bool clobbered = false;
+        for (const Wr &w : ws) {
+            if (w.step <= u.step - 4)
+                last = &w;
+            else if (w.step <= u.step)
+                clobbered = true;
+        }
+        CHECK(last && last->stripe == u.stripe - 1 && last->col == u.col && !clobbered,
+              "ring: G%d HR%d n%lld stripe %lld column %lld step %lld cap %lld dC %lld\n", G, HR, (long long)n,
+              (long long)u.stripe, (long long)u.col, (long long)u.step, (long long)cap, (long long)dC);
     }
     CHECK(holder_done >= 0 && holder_done < sc.s_end, "holder not done: G%d HR%d n%lld\n", G, HR, (long long)n);
 }

@@ -289,7 +289,8 @@ def test_batched_submit_and_poll_equal_one_by_one():
         assert [q for q, _ in one[rd.read_id]] == [q for q, _ in many[rd.read_id]]
         for (_, a), (_, b) in zip(one[rd.read_id], many[rd.read_id]):
             for f in a.dtype.names:
-                assert np.array_equal(a[f], b[f]), f
+                if f != "pad":  # padding is not part of the record's value
+                    assert np.array_equal(a[f], b[f]), f
             cells += int(b["cells"].sum())
     _check_against_oracle(pore, ref, ref_len, reads[:3], many)
     assert stats.flushes == 4 and stats.chunks == 40 and stats.cells == cells
