@@ -372,6 +372,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     b.d_events = take<float>(h, b, b.n_events);
     b.d_sig = take<SigDesc>(h, b, n_cands);
     b.d_r = take<float>(h, b, r_total);
+    b.n_r = r_total;
     b.d_work = take<WorkDesc>(h, b, b.n_work);
     b.d_results = take<rawalign_result_t>(h, b, n_cands);
     b.d_keys = take<unsigned long long>(h, b, n_reads);
@@ -470,6 +471,11 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
                 p.end_free = end_free;
                 p.early_term = b.et;
                 p.err = b.d_err;
+                p.n_events = b.n_events;
+                p.n_r = b.n_r;
+                p.n_fstore = 0;
+                p.n_results = (int)(b.anchored ? b.n_work : b.n_cands);
+                p.n_keys = (int)(b.anchored ? b.n_work : b.n_reads);
                 RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
                 ++launches;
                 RA_CUDA(cudaEventRecord(h->join[ci], cs));
@@ -826,6 +832,8 @@ extern "C" int rawalign_dtw_poll(rawalign_dtw_t *h, uint64_t ticket, rawalign_re
             RA_CUDA(cudaMemcpy(err, t.d_err, sizeof(err), cudaMemcpyDeviceToHost));
             if (err[1])
                 rc = RA_EINVAL;
+            else if (err[0])
+                rc = RA_EDEVICE;  // checked build: a work item failed its device-side checks
             uint32_t n = std::min<uint32_t>(cap, t.n);
             if (n && rc == RA_OK)
                 RA_CUDA(cudaMemcpy(out, t.d_results, sizeof(rawalign_result_t) * n, cudaMemcpyDeviceToHost));

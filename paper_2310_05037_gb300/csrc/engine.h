@@ -326,6 +326,7 @@ struct Batch {
     uint64_t slots = 0;          // planned lane-cell slots (sum of steps x G x HR)
     uint32_t n_reads = 0, n_cands = 0;
     uint64_t n_events = 0;
+    uint64_t n_r = 0;            // expected values in d_r
     std::vector<void *> blocks;  // arena allocations
     float *d_events = nullptr;
     SigDesc *d_sig = nullptr;

@@ -68,6 +68,10 @@ struct StripeParams {
     int end_free;                  // 1: FREE end (min over the last row)
     int *err;                      // error word (first failing work item + 1)
     int early_term;                // 1: branch and bound against the per-read best (GLOBAL end)
+    // extents the checked build tests every work item against (floats for
+    // the arrays, records for results and keys)
+    uint64_t n_events, n_r, n_fstore;
+    int n_results, n_keys;
 };
 
 // Anchor-guided alignment (Sec. 2.4.2): one candidate's cost is the sum, in

@@ -168,6 +168,12 @@ void reap(rawalign_dtw *h, ServeState *st, uint64_t fid, FlushRec *f)
     if (f->reaped)
         return;
     const bool reject = h->cfg.serve_early_reject && st->max_events > 0;
+#ifdef RAWALIGN_CHECKED
+    // checked build: a work item of this flush failed its device-side checks
+    const bool failed = f->n_items && ((const int *)(f->h_res + f->n_items))[0] != 0;
+#else
+    const bool failed = false;
+#endif
     for (auto &t : f->tickets) {
         std::vector<rawalign_result_t> v(f->h_res + t.first, f->h_res + t.first + t.count);
         const bool dead = reject && !t.last && t.count && v[0].decision == RA_PENDING &&
@@ -177,6 +183,8 @@ void reap(rawalign_dtw *h, ServeState *st, uint64_t fid, FlushRec *f)
             v[c].cand_idx = c;
             if ((t.last || dead) && v[c].decision == RA_PENDING)
                 v[c].decision = RA_UNMAPPED;
+            if (failed)
+                v[c].status = RA_EDEVICE;
         }
         st->ready[t.ticket] = std::move(v);
         st->ticket_flush.erase(t.ticket);
@@ -605,7 +613,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         ok = finalize_classes(h->sm_count, classes, take) == RA_OK;
     if (ok) {
         f->h_in = st->pinned.get(in_bytes);
-        f->h_res = (rawalign_result_t *)st->pinned.get(sizeof(rawalign_result_t) * std::max<uint32_t>(n_items, 1));
+        f->h_res = (rawalign_result_t *)st->pinned.get(sizeof(rawalign_result_t) * (n_items + 1));
         ok = f->h_in && f->h_res;
     }
     if (!ok) {
@@ -671,6 +679,11 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         p.b_match = h->cfg.b_match;
         p.end_free = 1;
         p.err = d_queue + kMaxClasses;
+        p.n_events = ev.size();
+        p.n_r = h->arena.size / sizeof(float);
+        p.n_fstore = h->arena.size / sizeof(float);
+        p.n_results = (int)n_items;
+        p.n_keys = (int)chunk_idx;
         RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
         RA_CUDA(cudaEventRecord(h->join[ci], cs));
         RA_CUDA(cudaStreamWaitEvent(s, h->join[ci], 0));
@@ -679,6 +692,10 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     RA_CUDA(cudaEventRecord(f->t_ev[2], s));
     f->n_items = n_items;
     RA_CUDA(cudaMemcpyAsync(f->h_res, f->d_res, sizeof(rawalign_result_t) * n_items, cudaMemcpyDeviceToHost, s));
+#ifdef RAWALIGN_CHECKED
+    // the kernels' error word travels back behind the results
+    RA_CUDA(cudaMemcpyAsync(f->h_res + n_items, d_queue + kMaxClasses, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+#endif
     RA_CUDA(cudaEventRecord(f->done, s));
     // launched: advance the host-side read state
     for (auto &u : updates) {

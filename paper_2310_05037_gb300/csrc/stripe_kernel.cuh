@@ -433,7 +433,28 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                     finish_lane();
                 } else {
                     const WorkDesc wd = p.work[tk];
-                    if (wd.s_end <= 0) {
+                    bool skip_item = false;
+#ifdef RAWALIGN_CHECKED
+                    // checked build: every planned extent lies inside its
+                    // array and the ring holds the item's period; a failing
+                    // item is reported in err[0] (first one, + 1) and skipped
+                    const bool bad =
+                        wd.nrows <= 0 || wd.m <= 0 || wd.ev_off + (uint64_t)wd.nrows > p.n_events ||
+                        wd.r_off + (uint64_t)wd.m > p.n_r || wd.cand < 0 || wd.cand >= p.n_results || wd.read < 0 ||
+                        wd.read >= p.n_keys || (wd.s_end > 0 && wd.dC + 2 > p.ring_cap) ||
+                        (wd.s_end > 0 && wd.fin_wid + kLaneLag * G + 4 > p.ring_cap) ||
+                        (wd.fin_off != ~0ull && wd.fin_off + (uint64_t)wd.fin_wid + 1 > p.n_fstore) ||
+                        (p.fstore_out && wd.fout_off > p.n_fstore);
+                    if (bad) {
+                        if (t == 0)
+                            atomicCAS(p.err, 0, tk + 1);
+                        have = false;
+                        skip_item = true;
+                    }
+#endif
+                    if (skip_item) {
+                        // nothing runs for this item; the group takes the next
+                    } else if (wd.s_end <= 0) {
                         // the band has no cell in the first row: nothing reaches the end
                         if (t == 0) {
                             rawalign_result_t *o = p.results + wd.cand;
