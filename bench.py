@@ -247,6 +247,8 @@ def make_workload(S, args, rank, name=None):
     name = name or args.workload
     if name in ("batched", "batched_et"):
         return S.config_batched(n_reads=args.reads, seed=0x5EED0002 + rank, true_first=name == "batched_et")
+    if name == "longread" and args.longread_reads != 2000:
+        return S.config_longread(n_reads=args.longread_reads, seed=0x5EED0005 + rank)
     return S.scaled(name, "full", seed=None if rank == 0 else 0x5EED1000 + rank)
 
 
@@ -400,6 +402,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
     ap.add_argument("--reads", type=int, default=20000, help="reads of the batched workload")
+    ap.add_argument("--longread-reads", type=int, default=2000, help="reads of the long-read workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -538,13 +541,13 @@ def main():
 
         als.close()
         # decision policy (Sec. 3.1) on reads whose loci have near-duplicates:
-        # 2 % of the reference's 5 kb blocks copied at 90 % identity, 25 % of
-        # the reads from a copied block with the copy among their candidates;
-        # event noise from the serving workload's sd 0.3 up to 0.6
+        # 2 % of the reference's 5 kb blocks copied at 98 % identity (as
+        # segmental duplications), 25 % of the reads from a copied block with
+        # the copy among their candidates; event noise sd 0.3 to 0.5
         study = {}
-        for sd in (0.3, 0.45, 0.6):
+        for sd in (0.3, 0.4, 0.5):
             pore_d, ref_d, rl_d, dreads = S.config_serving(seed=0x5EED0040, n_reads=512, noise_sd=sd, dup_frac=0.02,
-                                                           repeat_reads=0.25)
+                                                           repeat_reads=0.25, ident=0.98)
             ald = B.Aligner(pore_d, ref_d, rl_d, arena_bytes=len(ref_d) + (1 << 30), serve_slots=512,
                             serve_max_events=4000, max_candidates=32, device="cuda:%d" % local)
             try:
@@ -554,7 +557,7 @@ def main():
             study["noise_sd_%.2f" % sd] = decision_study(trs, [10.0, 20.0, 30.0, 40.0, 60.0], max_events=4000)
         out["served"] = {"closed_loop": closed, "realtime": rt,
                          "decision_study": {"reads": 512, "by_noise_and_threshold": study,
-                                            "workload": "512 reads per noise level, 2% of 5 kb blocks copied at 90% "
+                                            "workload": "512 reads per noise level, 2% of 5 kb blocks copied at 98% "
                                                         "identity, 25% of reads from a copied block with its copy "
                                                         "among the candidates, 50% off-target"},
                          "workload": "Read-Until serving: Poisson stream, 512 reads in flight, 180-event chunks, "

@@ -46,15 +46,17 @@ extern "C" {
 
 typedef struct rawalign_dtw rawalign_dtw_t; /* opaque handle */
 
+/* Status codes.  -7 is not used: serving has no cancel call (a read is
+ * stopped by closing it with an empty last chunk). */
 typedef enum {
     RA_OK = 0,
     RA_EINVAL = -1,     /* invalid argument or input data */
     RA_ENOMEM = -2,     /* the arena (or the frontier store) is too small */
     RA_EAGAIN = -3,     /* admission refused for now: retry after polling */
     RA_ENOTREADY = -4,  /* poll: the ticket has not completed yet */
-    RA_ETIMEDOUT = -5,  /* a bounded device wait gave up (per-result status) */
-    RA_EDEVICE = -6,    /* a CUDA call failed */
-    RA_ECANCELED = -7   /* the work was dropped (serving: read cancelled) */
+    RA_ETIMEDOUT = -5,  /* per-result status: a bounded wait between the warps that share one long
+                           alignment gave up (the result is not valid) */
+    RA_EDEVICE = -6     /* a CUDA call failed (checked build: a work item failed its checks) */
 } rawalign_status_t;
 
 enum { RA_END_GLOBAL = 0, RA_END_FREE = 1 };            /* end of the DTW */
@@ -63,12 +65,15 @@ enum { RA_UNMAPPED = 0, RA_MAPPED = 1, RA_PENDING = 2 };/* decision */
  * termination (config.early_termination); cost then holds a lower bound of
  * its cost, score the matching upper bound of its score, end = (-1,-1). */
 enum { RA_RESULT_PRUNED = 1 };
-/* kernel choice: AUTO picks a striped variant per alignment; PLAIN runs one
- * alignment per launch; RA_KERNEL_VARIANT0 + v forces striped variant v for
+/* kernel choice: AUTO picks a striped variant per alignment (and gives the
+ * few alignments that would outlast the rest of a batch on one warp to a
+ * block of four warps, each computing every fourth stripe); PLAIN runs one
+ * alignment per launch; SPLIT runs every alignment of a batch on a block of
+ * four warps (tests); RA_KERNEL_VARIANT0 + v forces striped variant v for
  * every alignment (tuning and tests): v = 0..9 are (lanes per alignment, rows
  * per lane) = (32,16) (16,16) (32,8) (16,8) (8,8) (4,8) (16,24) (8,24) (32,24)
  * (4,24). */
-enum { RA_KERNEL_AUTO = 0, RA_KERNEL_PLAIN = 1, RA_KERNEL_VARIANT0 = 16 };
+enum { RA_KERNEL_AUTO = 0, RA_KERNEL_PLAIN = 1, RA_KERNEL_SPLIT = 2, RA_KERNEL_VARIANT0 = 16 };
 
 typedef struct {
     int32_t k;                 /* k-mer length, 1..8; pore table has 4^k entries */
@@ -86,6 +91,10 @@ typedef struct {
     int32_t early_termination; /* 1: branch and bound in GLOBAL batches (Sec. 2.4.1), see prepare_batch */
     int32_t serve_early_reject;/* serving: 1 = decide RA_UNMAPPED as soon as no candidate can reach the
                                   threshold within serve_max_events events (see submit_chunk) */
+    int32_t test_stall_handoff;/* tests only, 0 otherwise: in the block-split kernel no stripe publishes
+                                  its bottom row, so the next stripe's bounded wait gives up and the
+                                  alignment's result comes back with status RA_ETIMEDOUT */
+    int32_t pad;
 } rawalign_dtw_config_t;
 
 /* One candidate region of the reference for one read (48 bytes). */
@@ -262,7 +271,7 @@ typedef struct {
     uint64_t cells;            /* in-band cells of the batch */
     uint64_t slots;            /* lane-cell slots the plan occupies (>= cells) */
     uint32_t launches;         /* kernels launched by one run */
-    uint32_t pad;
+    uint32_t split;            /* alignments run on a block of four warps (the longest ones) */
 } rawalign_dtw_stats_t;
 int rawalign_dtw_batch_stats(rawalign_dtw_t *h, uint64_t batch, rawalign_dtw_stats_t *out);
 

@@ -17,17 +17,17 @@ from .synth import ANCHOR_DTYPE, CANDIDATE_DTYPE
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librawalign_dtw.so")
 
-RA_OK, RA_EINVAL, RA_ENOMEM, RA_EAGAIN, RA_ENOTREADY, RA_ETIMEDOUT, RA_EDEVICE, RA_ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7
+RA_OK, RA_EINVAL, RA_ENOMEM, RA_EAGAIN, RA_ENOTREADY, RA_ETIMEDOUT, RA_EDEVICE = 0, -1, -2, -3, -4, -5, -6
 RA_END_GLOBAL, RA_END_FREE = 0, 1
 RA_UNMAPPED, RA_MAPPED, RA_PENDING = 0, 1, 2
 RA_RESULT_PRUNED = 1
-RA_KERNEL_AUTO, RA_KERNEL_PLAIN = 0, 1
+RA_KERNEL_AUTO, RA_KERNEL_PLAIN, RA_KERNEL_SPLIT = 0, 1, 2
 RA_KERNEL_VARIANT0 = 16
 VARIANTS = [(32, 16), (16, 16), (32, 8), (16, 8), (8, 8), (4, 8), (16, 24), (8, 24), (32, 24), (4, 24)]
 RA_KERNEL_STRIPE = {gh: RA_KERNEL_VARIANT0 + v for v, gh in enumerate(VARIANTS)}
 
 STATUS_NAMES = {0: "RA_OK", -1: "RA_EINVAL", -2: "RA_ENOMEM", -3: "RA_EAGAIN", -4: "RA_ENOTREADY",
-                -5: "RA_ETIMEDOUT", -6: "RA_EDEVICE", -7: "RA_ECANCELED"}
+                -5: "RA_ETIMEDOUT", -6: "RA_EDEVICE"}
 
 
 class RawAlignError(RuntimeError):
@@ -52,6 +52,8 @@ class Config(C.Structure):
         ("autotune_path", C.c_char_p),
         ("early_termination", C.c_int32),
         ("serve_early_reject", C.c_int32),
+        ("test_stall_handoff", C.c_int32),
+        ("pad", C.c_int32),
     ]
 
 
@@ -93,7 +95,7 @@ class Stats(C.Structure):
         ("cells", C.c_uint64),
         ("slots", C.c_uint64),
         ("launches", C.c_uint32),
-        ("pad", C.c_uint32),
+        ("split", C.c_uint32),
     ]
 
 
@@ -382,7 +384,7 @@ class Aligner:
     def __init__(self, pore, ref2bit, ref_len, arena_bytes=1 << 30, k=6, b_match=0.4, score_threshold=20.0,
                  end_mode=RA_END_GLOBAL, kernel=RA_KERNEL_AUTO, stream=None, serve_slots=0,
                  serve_max_events=0, max_candidates=64, device="cuda:0", autotune_path=None,
-                 early_termination=False, serve_early_reject=False):
+                 early_termination=False, serve_early_reject=False, test_stall_handoff=False):
         import torch
 
         self.torch = torch
@@ -404,6 +406,7 @@ class Aligner:
         cfg.serve_max_events = serve_max_events
         cfg.early_termination = 1 if early_termination else 0
         cfg.serve_early_reject = 1 if serve_early_reject else 0
+        cfg.test_stall_handoff = 1 if test_stall_handoff else 0
         self._tune_path = autotune_path.encode() if autotune_path else None
         cfg.autotune_path = self._tune_path
         self.cfg = cfg

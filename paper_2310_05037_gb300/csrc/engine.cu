@@ -350,13 +350,41 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     for (auto &pt_ : parts)
         b.max_rows = std::max(b.max_rows, pt_.max_rows);
     uint64_t slots[kNumVariants];
-    if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO)
-        shorten_longest(items, n_items, h->sm_count, h->slot_cost, slots, h->plan);
-    else
+    if (!b.plain && h->cfg.kernel == RA_KERNEL_AUTO) {
+        PlanParams pp = h->plan;
+        pp.split = !b.et;  // early termination checks run per group, not across a block
+        shorten_longest(items, n_items, h->sm_count, h->slot_cost, slots, pp);
+    } else {
+        if (h->cfg.kernel == RA_KERNEL_SPLIT) {
+            // every alignment on a block of four warps (tests)
+            parallel_for(n_items, [&](uint64_t x0, uint64_t x1) {
+                for (uint64_t x = x0; x < x1; ++x) {
+                    PlanItem &it = items[x];
+                    if (it.wd.s_end <= 0)
+                        continue;
+                    BandDef band;
+                    band.num = it.wd.num;
+                    band.den = it.wd.den;
+                    band.w = it.wd.w;
+                    band.m = it.wd.m;
+                    const Sched s24 = schedule(band, it.wd.row0, it.wd.nrows, 32, 24);
+                    if (s24.s_end <= 0)
+                        continue;
+                    it.variant = kSplitVariant;
+                    it.split = true;
+                    set_schedule(it, s24, h->plan.ring_bin_shift);
+                    it.cap = 128;
+                }
+            });
+        }
         variant_slots(items, n_items, slots);
+    }
     b.slots = 0;
     for (int v = 0; v < kNumVariants; ++v)
         b.slots += slots[v];
+    b.n_split = 0;
+    for (uint64_t x = 0; x < n_items; ++x)
+        b.n_split += items[x].split ? 1u : 0u;
     // launch order and classes (variant x ring size), longest first
     std::vector<int> &order = h->plan_order;
     b.classes.clear();
@@ -476,7 +504,11 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
                 p.n_fstore = 0;
                 p.n_results = (int)(b.anchored ? b.n_work : b.n_cands);
                 p.n_keys = (int)(b.anchored ? b.n_work : b.n_reads);
-                RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
+                p.stall_handoff = h->cfg.test_stall_handoff;
+                if (cl.split)
+                    RA_CUDA(launch_split(cl.HR, p, cl.grid, cs));
+                else
+                    RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs));
                 ++launches;
                 RA_CUDA(cudaEventRecord(h->join[ci], cs));
                 RA_CUDA(cudaStreamWaitEvent(s, h->join[ci], 0));
@@ -573,7 +605,7 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
         return RA_EINVAL;
     if (config->serve_slots < 0 || config->serve_max_events < 0 || config->max_candidates < 0)
         return RA_EINVAL;
-    if (config->kernel < RA_KERNEL_AUTO || config->kernel == 2 || config->kernel == 3 ||
+    if (config->kernel < RA_KERNEL_AUTO || config->kernel == 3 ||
         config->kernel >= RA_KERNEL_VARIANT0 + kNumVariants)
         return RA_EINVAL;
     const uint64_t n_pore = 1ull << (2 * config->k);
@@ -875,9 +907,9 @@ extern "C" int rawalign_dtw_batch_stats(rawalign_dtw_t *h, uint64_t batch, rawal
     out->dtw_ms = ms;
     out->total_ms = tot;
     out->cells = b.cells;
+    out->split = b.n_split;
     out->slots = b.slots;
     out->launches = b.launches;
-    out->pad = 0;
     return RA_OK;
 }
 

@@ -47,6 +47,7 @@ const int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}
                            {4, 24}};
 const double kSlotCost[] = {1.2107, 1.2336, 1.8882, 1.9132, 1.9968, 2.1240, 1.0095, 1.0287, 1.0, 1.0656};
 constexpr int kNumVariants = 10;
+constexpr int kSplitVariant = 8;  // (32, 24): the lane layout of the block-split kernel
 constexpr int kMaxClasses = 64;              // launches per run (variant x ring size)
 constexpr size_t kSmemRingLimit = 96 * 1024; // larger rings go to global memory
 
@@ -312,6 +313,7 @@ struct Arena {
 };
 
 struct ClassLaunch {
+    bool split = false;  // the block-split kernel: one alignment per block of four warps
     int G = 0, HR = 0;
     double max_cost = 0;       // lane-steps of the class's largest alignment (steps x lanes, empty as 0)
     int first = 0, count = 0;  // range in the sorted work array
@@ -327,6 +329,7 @@ struct Batch {
     uint32_t n_reads = 0, n_cands = 0;
     uint64_t n_events = 0;
     uint64_t n_r = 0;            // expected values in d_r
+    uint32_t n_split = 0;        // work items on the block-split kernel
     std::vector<void *> blocks;  // arena allocations
     float *d_events = nullptr;
     SigDesc *d_sig = nullptr;
@@ -374,6 +377,7 @@ struct PlanItem {
     int variant = 0;
     int cap = 0;        // ring entries the piece needs (power of two)
     double cost = 0;    // lane-steps: longest first
+    bool split = false; // runs on a whole block of four warps (split kernel)
 };
 
 // Scratch of the launch-order sort, kept by a handle across batches.
@@ -392,6 +396,7 @@ struct ServeState;
 struct PlanParams {
     int ring_bin_shift = 2;
     double latency_split = 0;
+    bool split = true;  // alignments longer than the batch on one warp go to the block-split kernel
 };
 
 }  // namespace ra_host
@@ -533,8 +538,8 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
         for (uint64_t x = lo; x < hi; ++x) {
             PlanItem &it = items[x];
             const int v0 = it.variant;
-            const double dur = (double)it.wd.s_end * kVariants[v0][1] * cost[v0];
-            if (it.wd.s_end <= 0 || kVariants[v0][0] == 32 || dur <= batch_len)
+            double dur = (double)it.wd.s_end * kVariants[v0][1] * cost[v0];
+            if (it.wd.s_end <= 0 || dur <= batch_len)
                 continue;
             BandDef band;
             band.num = it.wd.num;
@@ -542,24 +547,42 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
             band.w = it.wd.w;
             band.m = it.wd.m;
             int best = -1;
-            double best_score = -1;
             Sched best_s;
-            for (int v = 0; v < kNumVariants; ++v) {
-                if (kVariants[v][0] != 32)
-                    continue;
-                Sched s = schedule(band, it.wd.row0, it.wd.nrows, 32, kVariants[v][1]);
-                const double score = s.eff / cost[v];
-                if (s.s_end > 0 && score > best_score) {
-                    best_score = score;
-                    best = v;
-                    best_s = s;
+            if (kVariants[v0][0] != 32) {
+                double best_score = -1;
+                for (int v = 0; v < kNumVariants; ++v) {
+                    if (kVariants[v][0] != 32)
+                        continue;
+                    Sched s = schedule(band, it.wd.row0, it.wd.nrows, 32, kVariants[v][1]);
+                    const double score = s.eff / cost[v];
+                    if (s.s_end > 0 && score > best_score) {
+                        best_score = score;
+                        best = v;
+                        best_s = s;
+                    }
+                }
+                if (best >= 0 && (double)best_s.s_end * kVariants[best][1] * cost[best] >= dur)
+                    best = -1;
+                if (best >= 0)
+                    dur = (double)best_s.s_end * kVariants[best][1] * cost[best];
+            }
+            if (pp.split && dur > batch_len) {
+                // still longer than the batch on one warp: a block of four
+                // warps takes it (the split kernel's lanes hold 24 rows)
+                Sched s24 = schedule(band, it.wd.row0, it.wd.nrows, 32, 24);
+                if (s24.s_end > 0) {
+                    best = kSplitVariant;
+                    best_s = s24;
+                    it.split = true;
                 }
             }
-            if (best < 0 || (double)best_s.s_end * kVariants[best][1] * cost[best] >= dur)
+            if (best < 0)
                 continue;
             moved[v0] -= (int64_t)it.wd.s_end * kVariants[v0][0] * kVariants[v0][1];
             it.variant = best;
             set_schedule(it, best_s, pp.ring_bin_shift);
+            if (it.split)
+                it.cap = 128;  // not used by the split kernel: one class for all of them
             moved[best] += (int64_t)std::max(it.wd.s_end, 0) * kVariants[best][0] * kVariants[best][1];
             any = true;
         }
@@ -578,7 +601,7 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
 // are returned longest-alignment first.  Returns false if more than
 // kMaxClasses would be needed.
 inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &order, std::vector<ClassLaunch> &classes,
-                         SortScratch &scr)
+                         SortScratch &scr, bool longest_first = true)
 {
     // Launch order: a stable LSD radix sort (16-bit digits) on one 64-bit key
     // per item, the bucket (variant, ring size, wave) above the complemented
@@ -607,8 +630,11 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
     parallel_for(n, [&](uint64_t lo, uint64_t hi) {
         for (uint64_t x = lo; x < hi; ++x) {
             const PlanItem &it = items[x];
-            const uint64_t bucket = (uint64_t)((it.variant * kCaps + cap_index(it.cap)) * 2 + it.wave);
-            key[x] = bucket << 32 | (uint64_t)~(uint32_t)std::max(it.wd.s_end, 0);
+            const uint64_t bucket = (uint64_t)(((it.split ? 512 : 0) + it.variant * kCaps + cap_index(it.cap)) * 2 +
+                                               it.wave);
+            // without longest_first (serving flushes of similar pieces) the
+            // step counts do not take part in the order, only in max_cost
+            key[x] = bucket << 32 | (longest_first ? (uint64_t)~(uint32_t)std::max(it.wd.s_end, 0) : 0u);
             ord[x] = (int)x;
         }
     });
@@ -698,15 +724,19 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
     while (pos < n) {
         const PlanItem &f = items[ord[pos]];
         ClassLaunch cl;
+        cl.split = f.split;
         cl.G = kVariants[f.variant][0];
         cl.HR = kVariants[f.variant][1];
         cl.first = (int)pos;
         cl.ring_cap = f.cap;
         cl.max_cost = 0;
         const uint64_t id = key[pos] >> 33;
-        for (; pos < n && (key[pos] >> 33) == id; ++pos)
-            if ((int)pos == cl.first || (key[pos] >> 32) != (key[pos - 1] >> 32))
+        for (; pos < n && (key[pos] >> 33) == id; ++pos) {
+            if (!longest_first)
+                cl.max_cost = std::max(cl.max_cost, (double)std::max(items[ord[pos]].wd.s_end, 0) * cl.G);
+            else if ((int)pos == cl.first || (key[pos] >> 32) != (key[pos - 1] >> 32))
                 cl.max_cost = std::max(cl.max_cost, (double)(uint32_t)~(uint32_t)key[pos] * cl.G);
+        }
         cl.count = (int)pos - cl.first;
         classes.push_back(cl);
     }
@@ -717,10 +747,11 @@ inline bool make_classes(const PlanItem *items, size_t n, std::vector<int> &orde
     return true;
 }
 
-inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &order, std::vector<ClassLaunch> &classes)
+inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &order, std::vector<ClassLaunch> &classes,
+                         bool longest_first = true)
 {
     SortScratch scr;
-    const bool ok = make_classes(items.data(), items.size(), order, classes, scr);
+    const bool ok = make_classes(items.data(), items.size(), order, classes, scr, longest_first);
     order.resize(items.size());
     return ok;
 }
@@ -745,6 +776,17 @@ template <typename Alloc>
 int finalize_classes(int sm_count, std::vector<ClassLaunch> &classes, Alloc alloc)
 {
     for (auto &cl : classes) {
+        if (cl.split) {
+            // one alignment per block; the rings live in the kernel's own
+            // shared memory
+            const int nb = split_max_blocks_per_sm(cl.HR);
+            if (nb <= 0)
+                return RA_EDEVICE;
+            cl.ring_in_smem = 1;
+            cl.smem = split_smem_bytes();
+            cl.grid = std::max(1, std::min(sm_count * nb, cl.count));
+            continue;
+        }
         const int gpb = kBlock / cl.G;
         const size_t smem = (size_t)gpb * (cl.ring_cap + 1) * sizeof(float);
         cl.ring_in_smem = smem <= kSmemRingLimit;

@@ -72,6 +72,7 @@ struct StripeParams {
     // the arrays, records for results and keys)
     uint64_t n_events, n_r, n_fstore;
     int n_results, n_keys;
+    int stall_handoff;             // tests only: the split kernel's stripes never publish their bottom rows
 };
 
 // Anchor-guided alignment (Sec. 2.4.2): one candidate's cost is the sum, in
@@ -103,6 +104,11 @@ cudaError_t launch_check_events(const float *ev, uint64_t n, int *err, cudaStrea
 cudaError_t launch_stripe(int G, int HR, const StripeParams &p, int grid, int block, size_t smem,
                           cudaStream_t s);
 int stripe_max_blocks_per_sm(int G, int HR, int block, size_t smem);
+// the block-split kernel for long alignments (split_kernel.cu): four warps,
+// HR rows per lane, one alignment per block
+int split_max_blocks_per_sm(int HR);
+size_t split_smem_bytes();
+cudaError_t launch_split(int HR, const StripeParams &p, int grid, cudaStream_t s);
 void *pick_stripe_et(int G, int HR, bool smem_ring);  // stripe_kernel_et.cu
 cudaError_t launch_plain(const WorkDesc *w, const float *events, const float *r_all, float *diag,
                          rawalign_result_t *results, unsigned long long *best_keys, float b_match,

@@ -15,6 +15,7 @@
 // the GPU go into the next flush, and the stream orders the flushes, so a
 // read's chunk k+1 always sees the frontier chunk k wrote.  A read's memory
 // and slot are returned when the flush carrying its last chunk completes.
+#include <tuple>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -105,6 +106,16 @@ struct FlushRec {
     bool reaped = false;
 };
 
+// Shape of a serving piece for the variant cache: rows, band slope and
+// half-width, table width.
+struct ShapeKey {
+    int64_t rows, num, den, w, m;
+    bool operator<(const ShapeKey &o) const
+    {
+        return std::tie(rows, num, den, w, m) < std::tie(o.rows, o.num, o.den, o.w, o.m);
+    }
+};
+
 struct ServeState {
     int slots = 0;
     uint32_t max_events = 0;
@@ -119,6 +130,7 @@ struct ServeState {
     uint64_t next_flush = 1;
     PinnedPool pinned;
     std::vector<cudaEvent_t> timing_events;  // reusable timing events
+    std::map<ShapeKey, int> shape_variant;   // variant chosen per piece shape
     rawalign_dtw_serve_stats_t stats{};
 };
 
@@ -538,8 +550,21 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
                 if (sch.s_end <= 0)
                     it.variant = 0;
             } else {
-                it.variant = choose_variant(sc.band, row0, nrows, sch, h->slot_cost);
-                if (sch.s_end > 0) {
+                // candidates of one shape (chunk height, band, table width)
+                // share one choice across reads: a small handle-wide cache
+                const ShapeKey key{(int64_t)nrows, sc.band.num, sc.band.den, sc.band.w, sc.band.m};
+                auto hit = st->shape_variant.find(key);
+                if (hit != st->shape_variant.end()) {
+                    it.variant = hit->second;
+                    sch = schedule(sc.band, row0, nrows, kVariants[it.variant][0], kVariants[it.variant][1]);
+                } else {
+                    it.variant = choose_variant(sc.band, row0, nrows, sch, h->slot_cost);
+                    if (sch.s_end > 0 && st->shape_variant.size() < 4096)
+                        st->shape_variant[key] = it.variant;
+                }
+                if (sch.s_end <= 0) {
+                    it.variant = 0;
+                } else {
                     sc.plan_rows = nrows;
                     sc.plan_variant = it.variant;
                 }
@@ -586,7 +611,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     }
     std::vector<int> order;
     std::vector<ClassLaunch> classes;
-    if (!make_classes(items, order, classes)) {
+    if (!make_classes(items, order, classes, /*longest_first=*/false)) {
         delete f;
         return RA_EINVAL;
     }
