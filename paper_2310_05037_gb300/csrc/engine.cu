@@ -373,7 +373,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
                     it.variant = kSplitVariant;
                     it.split = true;
                     set_schedule(it, s24, h->plan.ring_bin_shift);
-                    it.cap = 128;
+                    it.cap = split_row_cap(it.wd);
                 }
             });
         }

@@ -481,6 +481,24 @@ inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &o
 
 inline int ring_need(const WorkDesc &wd, int G, int bin_shift = 2);
 
+// Floats of one bottom-row buffer of the block-split kernel (a power of two):
+// a stripe's last lane writes its columns from the stripe's first column - 32
+// to the band end of its last row, at most (H-1) num/den + 2w + 36 and at
+// most m + 33 values (H = 32 x 24 rows).
+inline int split_row_cap(const WorkDesc &wd)
+{
+    const int64_t H = 32 * 24;
+    int64_t need = (int64_t)wd.m + 33;
+    if (wd.den > 0) {
+        const int64_t banded = ((H - 1) * wd.num + wd.den - 1) / wd.den + 2 * (int64_t)wd.w + 36;
+        need = std::min(need, banded);
+    }
+    int64_t cap = 128;
+    while (cap < need)
+        cap <<= 1;
+    return (int)cap;
+}
+
 inline void set_schedule(PlanItem &it, const Sched &s, int bin_shift = 2)
 {
     it.wd.dC = s.dC;
@@ -582,7 +600,7 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
             it.variant = best;
             set_schedule(it, best_s, pp.ring_bin_shift);
             if (it.split)
-                it.cap = 128;  // not used by the split kernel: one class for all of them
+                it.cap = split_row_cap(it.wd);
             moved[best] += (int64_t)std::max(it.wd.s_end, 0) * kVariants[best][0] * kVariants[best][1];
             any = true;
         }
@@ -777,14 +795,19 @@ int finalize_classes(int sm_count, std::vector<ClassLaunch> &classes, Alloc allo
 {
     for (auto &cl : classes) {
         if (cl.split) {
-            // one alignment per block; the rings live in the kernel's own
-            // shared memory
+            // one alignment per block; each block's warps hand their bottom
+            // rows on through 2 buffers each of ring_cap floats in the arena
             const int nb = split_max_blocks_per_sm(cl.HR);
             if (nb <= 0)
                 return RA_EDEVICE;
-            cl.ring_in_smem = 1;
+            cl.ring_in_smem = 0;
             cl.smem = split_smem_bytes();
             cl.grid = std::max(1, std::min(sm_count * nb, cl.count));
+            while (!(cl.gring = (float *)alloc(sizeof(float) * (uint64_t)cl.grid * 4 * 2 * cl.ring_cap))) {
+                if (cl.grid == 1)
+                    return RA_ENOMEM;
+                cl.grid = (cl.grid + 1) / 2;
+            }
             continue;
         }
         const int gpb = kBlock / cl.G;

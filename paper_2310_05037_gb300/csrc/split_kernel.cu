@@ -5,16 +5,18 @@
 //
 // A 32-lane warp computes stripe k (H = 32 * HR rows; lane t owns HR rows and
 // runs one column behind lane t-1, taking lane t-1's bottom row by
-// __shfl_up_sync) while the next warp computes stripe k+1 a little behind it:
-// the bottom row of stripe k goes through a ring in shared memory from the
-// warp that writes it to the warp that reads it.  Each ring is a
-// single-producer single-consumer queue with two counters in shared memory:
-// the values written and the values read.  The reader waits until the value
-// it needs is written, the writer until its slot has been read; both waits
-// are bounded (about a third of a second of polling), and one that gives up
-// stops the alignment, whose result then carries RA_ETIMEDOUT.  All warps
-// wait only on warps of their own block, which are resident together, so
-// nothing waits on work that cannot run.
+// __shfl_up_sync) while the next warp computes stripe k+1 a little behind it.
+// The bottom row of stripe k goes from the warp that writes it to the warp
+// that reads it through a buffer in global memory (L2) that holds the whole
+// row, with a counter in shared memory: the stripe it belongs to and the
+// values written so far.  The reader waits until the value it needs is
+// written (a bounded wait: about a third of a second of polling, after which
+// the alignment stops and its result carries RA_ETIMEDOUT).  The writer never
+// waits: each warp has two buffers and alternates between them from one of
+// its stripes to the next, and stripe k+2W cannot start before stripe k+1 has
+// finished reading stripe k (stripe k+1 must finish before stripe k+W can,
+// which must finish before its warp starts stripe k+2W).  All waits are on
+// warps of the same block, which are resident together.
 //
 // Used for the few alignments so long that one warp alone would outlast the
 // rest of the batch (long reads): the planner gives each such alignment to a
@@ -28,25 +30,27 @@
 namespace ra {
 
 constexpr int kSplitWarps = 4;       // warps per block = stripes in flight
-constexpr int kSplitCap = 2048;      // ring entries (power of two) per warp pair
 constexpr int kSplitPublish = 8;     // the writer publishes its count every 8 values
+constexpr int kSplitAhead = 4;       // the reader fetches its row-above values 4 columns ahead
 constexpr unsigned kSpinLimit = 1u << 20;  // polls of a bounded wait (x 256 ns)
 
 struct SplitShared {
-    float ring[kSplitWarps][kSplitCap];
-    volatile int written[kSplitWarps];  // values the warp has written into its ring
-    volatile int read[kSplitWarps];     // values the next warp has read from that ring
-    volatile int abort;                 // a bounded wait gave up
+    // per warp and buffer: (stripe << 32) | values of its bottom row written
+    volatile unsigned long long tag[kSplitWarps][2];
+    volatile int abort;  // a bounded wait gave up
     unsigned long long cells;
     int item;
 };
 
-// Bounded wait of one lane until *ctr >= target (or the block aborts);
-// false when it gave up.
-static __device__ __forceinline__ bool wait_at_least(volatile int *ctr, int target, volatile int *abort)
+// Bounded wait of one lane until buffer tag *t says stripe `stripe` has more
+// than `idx` values (or the block aborts); false when it gave up.
+static __device__ __forceinline__ bool wait_written(volatile unsigned long long *t, int stripe, int idx,
+                                                    volatile int *abort)
 {
+    const unsigned long long want = ((unsigned long long)(unsigned)stripe << 32) | (unsigned)(idx + 1);
     for (unsigned it = 0; it < kSpinLimit; ++it) {
-        if (*ctr >= target) {
+        const unsigned long long v = *t;
+        if ((v >> 32) == (unsigned)stripe && v >= want) {
             __threadfence_block();  // the values behind the counter are visible
             return true;
         }
@@ -63,12 +67,13 @@ __global__ void __launch_bounds__(128, 4) dtw_split_kernel(const StripeParams p)
     constexpr int G = 32;
     constexpr int H = G * HR;
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int CM = kSplitCap - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SplitShared &sh = *reinterpret_cast<SplitShared *>(smem_raw);
     const int t = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int wprev = (w + kSplitWarps - 1) % kSplitWarps;
+    // this block's bottom-row buffers: [warp][2][ring_cap] floats
+    float *gbuf = p.gring + (size_t)blockIdx.x * kSplitWarps * 2 * p.ring_cap;
 
     while (true) {
         if (threadIdx.x == 0) {
@@ -76,10 +81,8 @@ __global__ void __launch_bounds__(128, 4) dtw_split_kernel(const StripeParams p)
             sh.abort = 0;
             sh.cells = 0;
         }
-        if (threadIdx.x < kSplitWarps) {
-            sh.written[threadIdx.x] = 0;
-            sh.read[threadIdx.x] = 0;
-        }
+        if (threadIdx.x < 2 * kSplitWarps)
+            sh.tag[threadIdx.x >> 1][threadIdx.x & 1] = ~0ull;  // no stripe yet
         __syncthreads();
         const int item = sh.item;
         if (item >= p.n_work)
@@ -118,7 +121,6 @@ __global__ void __launch_bounds__(128, 4) dtw_split_kernel(const StripeParams p)
         unsigned long long cells = 0;
         float best = kInf;
         int bestj = -1;
-        int wbase = 0, rbase = 0;  // sequence numbers: this warp's ring, the previous warp's ring
         bool aborted = false;
         for (int k = w; k < K && !aborted; k += kSplitWarps) {
             // ---- lane set-up for stripe k
@@ -181,7 +183,44 @@ __global__ void __launch_bounds__(128, 4) dtw_split_kernel(const StripeParams p)
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1)
                 S = max(S, __shfl_xor_sync(FULL, S, off));
-            int avail = 0, room = 0;  // reader: values known written; writer: sequence known free
+            // the buffer this stripe writes, and the one the previous stripe wrote
+            const int wb_ = (k / kSplitWarps) & 1, rb_ = ((k - 1) / kSplitWarps) & 1;
+            float *wbuf = gbuf + ((size_t)w * 2 + wb_) * p.ring_cap;
+            const float *rbuf = gbuf + ((size_t)wprev * 2 + rb_) * p.ring_cap;
+            volatile unsigned long long *wtag = &sh.tag[w][wb_];
+            volatile unsigned long long *rtag = &sh.tag[wprev][rb_];
+            if (t == G - 1 && k < K - 1) {
+                // starting a new row in this buffer (its last reader has finished)
+                *wtag = (unsigned long long)(unsigned)k << 32;
+            }
+            __syncwarp();
+            // lane 0's row above, fetched kSplitAhead columns ahead: q[x] holds
+            // the value of column j + 1 + x (0 for the virtual start, +inf
+            // outside the row above's band)
+            bool ok = true;
+            auto fetch = [&](int col) -> float {
+                if (k == 0)
+                    return col == -1 ? 0.f : kInf;
+                if ((unsigned)(col - loA) > widA)
+                    return kInf;
+                const int idx = col - rp0;
+                if (!wait_written(rtag, k - 1, idx, &sh.abort))
+                    ok = false;
+                return rbuf[idx];
+            };
+            float q0 = kInf, q1 = kInf, q2 = kInf, q3 = kInf;
+            if (t == 0) {
+                q0 = fetch(j + 1);
+                q1 = fetch(j + 2);
+                q2 = fetch(j + 3);
+                q3 = fetch(j + 4);
+            }
+            if (__any_sync(FULL, !ok)) {
+                if (t == 0)
+                    sh.abort = 1;
+                aborted = true;
+                break;
+            }
             float diag = kInf, bottom = kInf, vlast = kInf;
             unsigned ncells = 0;
             // ---- the stripe, one column per step
@@ -201,18 +240,13 @@ __global__ void __launch_bounds__(128, 4) dtw_split_kernel(const StripeParams p)
                 }
                 // lane 0's row above: the virtual cell D(-1,-1) = 0 for the
                 // first stripe, else the previous stripe's bottom row
-                float rc = kInf;
-                bool ok = true;
-                if (t == 0 && (unsigned)(j - loA) <= widA) {
-                    const int seq = rbase + (j - rp0);
-                    if (seq >= avail) {
-                        ok = wait_at_least(&sh.written[wprev], seq + 1, &sh.abort);
-                        avail = sh.written[wprev];
-                    }
-                    rc = sh.ring[wprev][seq & CM];
+                const float rc = q0;
+                if (t == 0) {
+                    q0 = q1;
+                    q1 = q2;
+                    q2 = q3;
+                    q3 = fetch(j + kSplitAhead);
                 }
-                if (t == 0 && k == 0)
-                    rc = (j == -1) ? 0.f : kInf;
                 if (__any_sync(FULL, !ok)) {
                     aborted = true;
                     break;
@@ -253,25 +287,12 @@ __global__ void __launch_bounds__(128, 4) dtw_split_kernel(const StripeParams p)
                             vlast = D[r];
                 }
                 if (writer) {
-                    const int seq = wbase + (j - wp0);
-                    if (seq >= room) {
-                        ok = wait_at_least(&sh.read[w], seq + 1 - kSplitCap, &sh.abort);
-                        room = sh.read[w] + kSplitCap;
-                    }
-                    sh.ring[w][seq & CM] = bottom;
-                    if (((seq + 1) % kSplitPublish) == 0 && !p.stall_handoff) {
+                    const int idx = j - wp0;
+                    wbuf[idx] = bottom;
+                    if (((idx + 1) % kSplitPublish) == 0 && !p.stall_handoff) {
                         __threadfence_block();
-                        sh.written[w] = seq + 1;
+                        *wtag = ((unsigned long long)(unsigned)k << 32) | (unsigned)(idx + 1);
                     }
-                }
-                if (__any_sync(FULL, !ok)) {
-                    aborted = true;
-                    break;
-                }
-                if (t == 0 && k > 0 && (((j - rp0 + 1) % kSplitPublish) == 0)) {
-                    // the values up to this column are read
-                    __threadfence_block();
-                    sh.read[wprev] = rbase + (j - rp0) + 1;
                 }
             }
             if (aborted) {
@@ -280,16 +301,10 @@ __global__ void __launch_bounds__(128, 4) dtw_split_kernel(const StripeParams p)
                 break;
             }
             cells += ncells;
-            // end of the stripe: publish everything written and read
-            const int wrote = k < K - 1 ? run_len(k) : 0;
-            const int readn = k > 0 ? run_len(k - 1) : 0;
+            // end of the stripe: publish the whole bottom row
             __threadfence_block();
             if (t == G - 1 && k < K - 1 && !p.stall_handoff)
-                sh.written[w] = wbase + wrote;
-            if (t == 0 && k > 0)
-                sh.read[wprev] = rbase + readn;
-            wbase += wrote;
-            rbase += readn;
+                *wtag = ((unsigned long long)(unsigned)k << 32) | (unsigned)run_len(k);
             if (holds_last) {
                 const float v = vlast;
                 float cost;
