@@ -65,9 +65,10 @@ enum { RA_UNMAPPED = 0, RA_MAPPED = 1, RA_PENDING = 2 };/* decision */
  * termination (config.early_termination); cost then holds a lower bound of
  * its cost, score the matching upper bound of its score, end = (-1,-1). */
 enum { RA_RESULT_PRUNED = 1 };
-/* kernel choice: AUTO picks a striped variant per alignment (and gives the
- * few alignments that would outlast the rest of a batch on one warp to a
- * block of four warps, each computing every fourth stripe); PLAIN runs one
+/* kernel choice: AUTO picks a striped variant per alignment (and, when the
+ * tuning file's "block_split X" is above 0, gives the alignments that would
+ * take over X times the batch's balanced length on one warp to a block of
+ * four warps, each computing every fourth stripe); PLAIN runs one
  * alignment per launch; SPLIT runs every alignment of a batch on a block of
  * four warps (tests); RA_KERNEL_VARIANT0 + v forces striped variant v for
  * every alignment (tuning and tests): v = 0..9 are (lanes per alignment, rows
@@ -227,6 +228,7 @@ typedef struct {
     double h2d_ms;             /* device time of the input copies */
     double device_ms;          /* device time from the first kernel to the last */
     double d2h_ms;             /* device time of the result copy */
+    double host_launch_ms;     /* the part of host_flush_ms spent in CUDA calls (copies, launches, events) */
 } rawalign_dtw_serve_stats_t;
 int rawalign_dtw_serve_stats(rawalign_dtw_t *h, rawalign_dtw_serve_stats_t *out, int reset);
 
@@ -308,10 +310,11 @@ int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_events, const f
  * autotuner measures these costs.  config.autotune_path may name a text file
  * of "G HR cost" lines with the same numbers, and the planner's bin edges:
  * "ring_bins S" (S = 2: launch classes bin ring sizes by powers of four, the
- * default; S = 1: by powers of two) and "latency_split X" (an alignment
+ * default; S = 1: by powers of two), "latency_split X" (an alignment
  * longer than X times the batch's estimated length moves to a 32-lane
- * variant; 0 = automatic); create returns RA_EINVAL for other values.  None
- * of these change results, only the launch plan.  Returns RA_EINVAL for a
+ * variant; 0 = automatic) and "block_split X" (see RA_KERNEL_AUTO; 0, the
+ * default, = never); create returns RA_EINVAL for other values.  None of
+ * these change results, only the launch plan.  Returns RA_EINVAL for a
  * wrong count or a non-positive cost. */
 int rawalign_dtw_set_variant_costs(rawalign_dtw_t *h, const double *costs, uint32_t n);
 

@@ -89,10 +89,11 @@ def tune(device="cuda:0", runs=3, sm_count=None, groups_factor=4, verbose=False,
 
 
 def tune_plan(workload, costs=None, device="cuda:0", runs=3, ring_bins=(2, 1), latency_splits=(0.0, 0.5, 1.0, 2.0),
-              arena_bytes=None):
+              block_splits=(None,), arena_bytes=None):
     """Chooses the planner's bin edges on a sample batch (a synth.Workload):
-    every (ring_bins, latency_split) pair is timed (best of `runs` replays of
-    the DTW part); returns (best {"ring_bins", "latency_split"}, {pair: ms})."""
+    every (ring_bins, latency_split, block_split) choice is timed (best of
+    `runs` replays of the DTW part; block_split None = the library's default);
+    returns (best {"ring_bins", "latency_split"[, "block_split"]}, {choice: ms})."""
     w = workload
     if arena_bytes is None:
         m_total = int(np.sum(w.cands["ref_len_bases"].astype(np.int64) - w.k + 1))
@@ -100,10 +101,13 @@ def tune_plan(workload, costs=None, device="cuda:0", runs=3, ring_bins=(2, 1), l
             len(w.ref2bit) + (512 << 20)
     times = {}
     with tempfile.TemporaryDirectory() as d:
-        for rb in ring_bins:
-            for ls in latency_splits:
-                path = os.path.join(d, "t_%d_%g.txt" % (rb, ls))
-                write_table(path, costs or {}, {"ring_bins": rb, "latency_split": ls})
+        for rb, ls, bs in [(rb, ls, bs) for rb in ring_bins for ls in latency_splits for bs in block_splits]:
+            if True:
+                path = os.path.join(d, "t_%d_%g_%s.txt" % (rb, ls, bs))
+                knobs = {"ring_bins": rb, "latency_split": ls}
+                if bs is not None:
+                    knobs["block_split"] = bs
+                write_table(path, costs or {}, knobs)
                 al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena_bytes, k=w.k, device=device,
                                autotune_path=path)
                 try:
@@ -114,12 +118,15 @@ def tune_plan(workload, costs=None, device="cuda:0", runs=3, ring_bins=(2, 1), l
                         al.poll(al.run(b), 0)
                         ms = al.stats(b).dtw_ms
                         best = ms if best is None else min(best, ms)
-                    times[(rb, ls)] = best
+                    times[(rb, ls) if bs is None else (rb, ls, bs)] = best
                     al.release(b)
                 finally:
                     al.close()
-    (rb, ls) = min(times, key=times.get)
-    return {"ring_bins": rb, "latency_split": ls}, times
+    best = min(times, key=times.get)
+    plan = {"ring_bins": best[0], "latency_split": best[1]}
+    if len(best) > 2:
+        plan["block_split"] = best[2]
+    return plan, times
 
 
 def write_table(path, costs, plan=None):
@@ -132,6 +139,8 @@ def write_table(path, costs, plan=None):
                 f.write("ring_bins %d\n" % int(plan["ring_bins"]))
             if "latency_split" in plan:
                 f.write("latency_split %.6f\n" % float(plan["latency_split"]))
+            if "block_split" in plan:
+                f.write("block_split %.6f\n" % float(plan["block_split"]))
 
 
 def read_table(path):
@@ -143,8 +152,8 @@ def read_table(path):
             costs[(int(parts[0]), int(parts[1]))] = float(parts[2])
         elif len(parts) == 2 and parts[0] == "ring_bins":
             plan["ring_bins"] = int(parts[1])
-        elif len(parts) == 2 and parts[0] == "latency_split":
-            plan["latency_split"] = float(parts[1])
+        elif len(parts) == 2 and parts[0] in ("latency_split", "block_split"):
+            plan[parts[0]] = float(parts[1])
     return costs, plan
 
 

@@ -110,6 +110,7 @@ class ServeStats(C.Structure):
         ("h2d_ms", C.c_double),
         ("device_ms", C.c_double),
         ("d2h_ms", C.c_double),
+        ("host_launch_ms", C.c_double),
     ]
 
 

@@ -645,6 +645,11 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
                     h->plan.latency_split = c;
                 else
                     bad = true;
+            } else if (sscanf(line, " block_split %lf", &c) == 1) {
+                if (std::isfinite(c) && c >= 0)
+                    h->plan.split_factor = c;
+                else
+                    bad = true;
             }
         }
         fclose(f);

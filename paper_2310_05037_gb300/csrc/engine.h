@@ -396,7 +396,11 @@ struct ServeState;
 struct PlanParams {
     int ring_bin_shift = 2;
     double latency_split = 0;
-    bool split = true;  // alignments longer than the batch on one warp go to the block-split kernel
+    bool split = true;          // the block-split kernel may be used (not with early termination)
+    double split_factor = 0.0;  // "block_split X": an alignment whose time on one warp exceeds X times
+                                // the batch's balanced length (its work over all resident lanes)
+                                // goes to a block of four warps; 0 = never (the default: on the
+                                // long-read workload it measured slower, see the design notes)
 };
 
 }  // namespace ra_host
@@ -557,7 +561,8 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
             PlanItem &it = items[x];
             const int v0 = it.variant;
             double dur = (double)it.wd.s_end * kVariants[v0][1] * cost[v0];
-            if (it.wd.s_end <= 0 || dur <= batch_len)
+            const double split_len = pp.split_factor * total / (512.0 * std::max(sm_count, 1));
+            if (it.wd.s_end <= 0 || dur <= std::min(batch_len, pp.split && pp.split_factor > 0 ? split_len : batch_len))
                 continue;
             BandDef band;
             band.num = it.wd.num;
@@ -584,7 +589,8 @@ inline void shorten_longest(PlanItem *items, size_t n, int sm_count, const doubl
                 if (best >= 0)
                     dur = (double)best_s.s_end * kVariants[best][1] * cost[best];
             }
-            if (pp.split && dur > batch_len) {
+            // the balanced length: the batch's work spread over every resident lane
+            if (pp.split && pp.split_factor > 0 && dur > split_len) {
                 // still longer than the batch on one warp: a block of four
                 // warps takes it (the split kernel's lanes hold 24 rows)
                 Sched s24 = schedule(band, it.wd.row0, it.wd.nrows, 32, 24);

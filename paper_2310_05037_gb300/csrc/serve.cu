@@ -665,6 +665,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     memcpy(hin + o_rd, read_of.data(), b_rd);
     memset(hin + o_keys, 0, in_bytes - o_keys);
     cudaStream_t s = h->stream;
+    const auto t_launch = std::chrono::steady_clock::now();
     // timing events (start, inputs copied, kernels done, done), reused
     while (st->timing_events.size() < 4) {
         cudaEvent_t e = nullptr;
@@ -735,6 +736,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         rd.signal_done = true;
         rd.rows_done += (uint32_t)pc.ev.size();
     }
+    st->stats.host_launch_ms += ms_since(t_launch);
     st->stats.flushes++;
     st->stats.chunks += chunk_idx;
     st->stats.pieces += n_items;

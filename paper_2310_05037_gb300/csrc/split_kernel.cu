@@ -56,7 +56,8 @@ static __device__ __forceinline__ bool wait_written(volatile unsigned long long 
         }
         if (*abort)
             return false;
-        __nanosleep(256);
+        if (it >= 32)
+            __nanosleep(256);  // poll without sleeping first: the writer is usually a few steps away
     }
     return false;
 }

@@ -44,11 +44,19 @@ def test_split_forced_workloads(name):
 
 
 def test_planner_splits_long_reads():
-    """A long-read batch with few alignments: the planner gives the longest
-    to the split kernel (the batch counters say how many), and every result
-    is the oracle's."""
+    """A long-read batch with few alignments and the tuning file's
+    block_split on: the planner gives the longest alignments to the split
+    kernel (the batch counters say how many), and every result is the
+    oracle's."""
+    import os
+    import tempfile
+
+    from paper_2310_05037_gb300 import autotune as T
+
     w = S.config_longread(n_reads=12, ref_len=4_000_000, nmin=8000, nmax=16000)
-    al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena_bytes_for(w) + (1 << 30))
+    path = os.path.join(tempfile.mkdtemp(), "tune.txt")
+    T.write_table(path, {}, {"block_split": 1.0})
+    al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena_bytes_for(w) + (1 << 30), autotune_path=path)
     try:
         b = al.prepare(w.events, w.read_offsets, w.cands)
         got = al.poll(al.run(b), w.n_cands)
