@@ -541,13 +541,13 @@ def main():
 
         als.close()
         # decision policy (Sec. 3.1) on reads whose loci have near-duplicates:
-        # 2 % of the reference's 5 kb blocks copied at 98 % identity (as
+        # 2 % of the reference's 20 kb blocks copied at 98 % identity (as
         # segmental duplications), 25 % of the reads from a copied block with
         # the copy among their candidates; event noise sd 0.3 to 0.5
         study = {}
         for sd in (0.3, 0.4, 0.5):
             pore_d, ref_d, rl_d, dreads = S.config_serving(seed=0x5EED0040, n_reads=512, noise_sd=sd, dup_frac=0.02,
-                                                           repeat_reads=0.25, ident=0.98)
+                                                           repeat_reads=0.25, ident=0.98, block=20000)
             ald = B.Aligner(pore_d, ref_d, rl_d, arena_bytes=len(ref_d) + (1 << 30), serve_slots=512,
                             serve_max_events=4000, max_candidates=32, device="cuda:%d" % local)
             try:
@@ -557,7 +557,7 @@ def main():
             study["noise_sd_%.2f" % sd] = decision_study(trs, [10.0, 20.0, 30.0, 40.0, 60.0], max_events=4000)
         out["served"] = {"closed_loop": closed, "realtime": rt,
                          "decision_study": {"reads": 512, "by_noise_and_threshold": study,
-                                            "workload": "512 reads per noise level, 2% of 5 kb blocks copied at 98% "
+                                            "workload": "512 reads per noise level, 2% of 20 kb blocks copied at 98% "
                                                         "identity, 25% of reads from a copied block with its copy "
                                                         "among the candidates, 50% off-target"},
                          "workload": "Read-Until serving: Poisson stream, 512 reads in flight, 180-event chunks, "

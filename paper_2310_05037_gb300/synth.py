@@ -487,9 +487,13 @@ def config_serving(seed: int = 0x5EED0004, n_reads: int = 2048, ref_len: int = 1
         n_dup = max(1, int(dup_frac * n_blocks))
         dst = rng.choice(n_blocks, size=n_dup, replace=False)
         srcs = rng.integers(0, n_blocks, size=n_dup)
+        is_dst = np.zeros(n_blocks, bool)
+        is_dst[dst] = True
         for d, sb in zip(dst.tolist(), srcs.tolist()):
-            if d == sb:
-                continue
+            # a source block is never itself overwritten, so every copy
+            # stays a near-duplicate of its source
+            while is_dst[sb]:
+                sb = int(rng.integers(0, n_blocks))
             codes = unpack_bases(ref, sb * block, block).copy()
             mut = rng.random(block) < (1.0 - ident)
             codes[mut] = (codes[mut] + rng.integers(1, 4, size=int(mut.sum()))).astype(np.uint8) & 3
@@ -498,6 +502,9 @@ def config_serving(seed: int = 0x5EED0004, n_reads: int = 2048, ref_len: int = 1
     # a read from a copied block walks 2 * max_events + K bases from its start
     walk_len = 2 * max_events + K
     fits = block - max(span, walk_len)
+    if repeat_reads > 0 and dup_frac > 0 and fits <= 0:
+        raise ValueError("repeat_reads needs blocks longer than a read's walk (%d bases) and its "
+                         "candidate span (%d)" % (walk_len, span))
     out = []
     t = 0.0
     for q in range(n_reads):
