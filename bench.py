@@ -60,9 +60,11 @@ WORKLOADS = {
 METRIC = "DTW GCUPS and reads/s (batched and served vs plain per-alignment kernel); p50/p99 chunk latency"
 OPS_PER_CELL = 4  # sub, min, min, add per DP cell
 # ALU-pipe lane-slots per in-band cell of the striped kernel's hot loop: the
-# 3-input min (issued at half rate: 2 slots) and the band-mask bit test and
-# select (1 + 1); the subtraction and the addition go to the FMA pipe.
-ALU_SLOTS_PER_CELL = 4.0
+# 3-input min (issued at half rate: 2 slots), the select of the row's event
+# by the band mask with its share of the mask-to-predicate moves (1.15), the
+# per-column work spread over the lane's 24 rows (about 0.35) and the stripe
+# changes (about 0.1); the subtraction and the addition go to the FMA pipe.
+ALU_SLOTS_PER_CELL = 3.6
 # DRAM bytes (read + write) of the DTW part of one step of a workload, from an
 # ncu capture of the current kernel (None: not captured for this kernel).
 TRAFFIC = {}

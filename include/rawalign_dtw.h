@@ -229,6 +229,8 @@ typedef struct {
     double device_ms;          /* device time from the first kernel to the last */
     double d2h_ms;             /* device time of the result copy */
     double host_launch_ms;     /* the part of host_flush_ms spent in CUDA calls (copies, launches, events) */
+    double host_plan_ms;       /* the part of host_flush_ms spent planning the pieces and packing the inputs */
+    double host_reap_ms;       /* taking finished flushes' results (in flush and in the polls) */
 } rawalign_dtw_serve_stats_t;
 int rawalign_dtw_serve_stats(rawalign_dtw_t *h, rawalign_dtw_serve_stats_t *out, int reset);
 

@@ -111,6 +111,8 @@ class ServeStats(C.Structure):
         ("device_ms", C.c_double),
         ("d2h_ms", C.c_double),
         ("host_launch_ms", C.c_double),
+        ("host_plan_ms", C.c_double),
+        ("host_reap_ms", C.c_double),
     ]
 
 

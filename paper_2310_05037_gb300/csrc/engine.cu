@@ -248,13 +248,16 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
             int64_t n = -1, num = 0, den = 0, w = 0, m = 0;
             int variant = 0;
             Sched sc;
+            uint64_t cells = 0;
         };
         std::vector<Choice> cache(1024);
         auto schedule_item = [&](PlanItem &it, const BandDef &band, int64_t n) {
             Sched sc;
+            uint64_t cells = 0;
             if (b.plain || (forced >= 0 && forced < kNumVariants)) {
                 it.variant = b.plain ? 0 : forced;
                 sc = schedule(band, 0, n, kVariants[it.variant][0], kVariants[it.variant][1]);
+                cells = band_cells(band, 0, n);
             } else {
                 const uint64_t hk = ((uint64_t)n * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)band.m * 0xC2B2AE3D27D4EB4Full) ^
                                     ((uint64_t)band.w * 0x165667B19E3779F9ull) ^ ((uint64_t)band.num << 17) ^
@@ -263,8 +266,10 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
                 if (ch.n == n && ch.m == band.m && ch.w == band.w && ch.num == band.num && ch.den == band.den) {
                     it.variant = ch.variant;
                     sc = ch.sc;
+                    cells = ch.cells;
                 } else {
                     it.variant = choose_variant(band, 0, n, sc, h->slot_cost);
+                    cells = band_cells(band, 0, n);
                     ch.n = n;
                     ch.m = band.m;
                     ch.w = band.w;
@@ -272,10 +277,13 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
                     ch.den = band.den;
                     ch.variant = it.variant;
                     ch.sc = sc;
+                    ch.cells = cells;
                 }
             }
             it.wave = 0;
             set_schedule(it, sc, h->plan.ring_bin_shift);
+            // the striped kernel reports this count instead of counting
+            it.wd.cells = sc.s_end > 0 ? cells : 0;
             pt_.max_rows = std::max<int>(pt_.max_rows, (int)n);
         };
         uint64_t ix = pt_.ib, px = pt_.pb, rx = pt_.rb;

@@ -177,9 +177,92 @@ inline int64_t cdiv(int64_t a, int64_t b) { return -fdiv(-a, b); }
 
 struct BandDef {
     int64_t num = 0, den = 1, w = 0, m = 1;
+    int64_t per = 0;  // den / gcd(num, den) when known (0: not computed), see band_cells
     int64_t lo(int64_t i) const { return std::max<int64_t>(0, cdiv(i * num - w * den, den)); }
     int64_t hi(int64_t i) const { return std::min<int64_t>(m - 1, fdiv(i * num + w * den, den)); }
 };
+
+// sum_{i=0}^{n-1} floor((a i + b) / c) for n, a, b >= 0 and c > 0, in
+// O(log c) steps: whole multiples of c in a and b are summed directly, and
+// with a, b < c the sum counts the lattice points under the line, which is
+// the same kind of sum with the roles of a and c exchanged (the Euclidean
+// reduction of the floor sum).
+inline uint64_t floor_sum(uint64_t n, uint64_t c, uint64_t a, uint64_t b)
+{
+    unsigned __int128 acc = 0;
+    while (n > 0) {
+        if (a >= c) {
+            acc += (unsigned __int128)(n * (n - 1) / 2) * (a / c);
+            a %= c;
+        }
+        if (b >= c) {
+            acc += (unsigned __int128)n * (b / c);
+            b %= c;
+        }
+        // points (i, k) with k >= 1 and k c <= a i + b: per k, the rows
+        // i >= (k c - b) / a; rewritten as a floor sum over k of (c k' + y % c) / a
+        if (a <= (UINT64_MAX - b) / n) {
+            const uint64_t y = a * n + b;
+            if (y < c)
+                break;
+            n = y / c;
+            b = y % c;
+        } else {
+            const unsigned __int128 y = (unsigned __int128)a * n + b;
+            n = (uint64_t)(y / c);
+            b = (uint64_t)(y % c);
+        }
+        std::swap(a, c);
+    }
+    return (uint64_t)acc;
+}
+
+// In-band cells of rows [r0, r1) of a band (the table's cells (i, j) with
+// lo(i) <= j <= hi(i)), exactly, in O(log den): the sums of hi and of lo over
+// the rows are floor sums between the rows where the band meets the table's
+// edges.  Rows whose band starts past the last column hold no cell.
+inline uint64_t band_cells(const BandDef &b, int64_t r0, int64_t r1)
+{
+    if (r1 <= r0)
+        return 0;
+    if (b.num == 0)
+        return (uint64_t)(r1 - r0) * (uint64_t)(b.hi(0) - b.lo(0) + 1);
+    // rows with lo(i) <= m - 1: i num - w den <= (m - 1) den
+    r1 = std::min<int64_t>(r1, fdiv((b.m - 1 + b.w) * b.den, b.num) + 1);
+    if (r1 <= r0)
+        return 0;
+    const uint64_t num = (uint64_t)b.num, den = (uint64_t)b.den, wd = (uint64_t)(b.w * b.den);
+    // sum of hi: floor((i num + w den) / den) below i_h, m - 1 from i_h on
+    const int64_t i_h = std::max<int64_t>(0, cdiv((b.m - 1 - b.w) * b.den, b.num));
+    if (b.per > 0 && r1 <= i_h && r0 * b.num >= b.w * b.den - b.den + 1) {
+        // no row of the range meets an edge of the table: with x = i num / den,
+        // hi - lo + 1 = floor(x + w) - ceil(x - w) + 1 = 2w + [x is whole],
+        // and x is whole exactly on the multiples of den / gcd(num, den)
+        const uint64_t whole = (uint64_t)(fdiv(r1 - 1, b.per) - fdiv(r0 - 1, b.per));
+        return (uint64_t)(r1 - r0) * (uint64_t)(2 * b.w) + whole;
+    }
+    uint64_t s_hi = 0;
+    {
+        const int64_t a = r0, e = std::min(r1, std::max(r0, i_h));
+        if (e > a)
+            s_hi += floor_sum((uint64_t)e, den, num, wd) - floor_sum((uint64_t)a, den, num, wd);
+        const int64_t a2 = std::max(r0, i_h);
+        if (r1 > a2)
+            s_hi += (uint64_t)(r1 - a2) * (uint64_t)(b.m - 1);
+    }
+    // sum of lo: 0 up to i_l, from i_l on ceil((i num - w den) / den) >= 1,
+    // a floor sum over t = i - i_l with offset i_l num - w den + den - 1 >= den
+    const int64_t i_l = fdiv(b.w * b.den, b.num) + 1;
+    uint64_t s_lo = 0;
+    {
+        const int64_t a = std::max(r0, i_l);
+        if (r1 > a) {
+            const uint64_t off = (uint64_t)(i_l * b.num - b.w * b.den + b.den - 1);
+            s_lo = floor_sum((uint64_t)(r1 - i_l), den, num, off) - floor_sum((uint64_t)(a - i_l), den, num, off);
+        }
+    }
+    return s_hi - s_lo + (uint64_t)(r1 - r0);
+}
 
 // Band of one candidate (Sec. 2.4.3): derived slope (m-1)/(n-1) unless given;
 // w_eff = max(w, ceil(num/(2 den)), 1); no band -> num 0, den 1, w = m.

@@ -39,7 +39,7 @@ struct WorkDesc {
     int32_t w_report;   // w_eff reported in the result (-1 = no band)
     int32_t a0;         // first in-band column of row0
     int32_t s_end;      // steps until the group is done (<= 0: no in-band cell)
-    int32_t pad0, pad1;
+    uint64_t cells;     // in-band cells of the piece (the host counts them exactly)
 };
 static_assert(sizeof(WorkDesc) == 112, "WorkDesc layout");
 

@@ -15,6 +15,7 @@
 // the GPU go into the next flush, and the stream orders the flushes, so a
 // read's chunk k+1 always sees the frontier chunk k wrote.  A read's memory
 // and slot are returned when the flush carrying its last chunk completes.
+#include <numeric>
 #include <tuple>
 #include <unordered_map>
 #include <unordered_set>
@@ -131,6 +132,7 @@ struct ServeState {
     PinnedPool pinned;
     std::vector<cudaEvent_t> timing_events;  // reusable timing events
     std::map<ShapeKey, int> shape_variant;   // variant chosen per piece shape
+    std::mutex shape_mu;                     // guards shape_variant while a flush plans in parallel
     rawalign_dtw_serve_stats_t stats{};
 };
 
@@ -175,10 +177,13 @@ bool unreachable(const rawalign_result_t *r, uint32_t n, float b_match, uint32_t
     return true;
 }
 
+double ms_since(std::chrono::steady_clock::time_point t0);
+
 void reap(rawalign_dtw *h, ServeState *st, uint64_t fid, FlushRec *f)
 {
     if (f->reaped)
         return;
+    const auto t_reap = std::chrono::steady_clock::now();
     const bool reject = h->cfg.serve_early_reject && st->max_events > 0;
 #ifdef RAWALIGN_CHECKED
     // checked build: a work item of this flush failed its device-side checks
@@ -229,6 +234,7 @@ void reap(rawalign_dtw *h, ServeState *st, uint64_t fid, FlushRec *f)
     f->reaped = true;
     st->flushes.erase(fid);
     delete f;
+    st->stats.host_reap_ms += ms_since(t_reap);
 }
 
 void reap_done(rawalign_dtw *h, ServeState *st)
@@ -352,6 +358,8 @@ int submit_one(rawalign_dtw *h, ServeState *st, uint64_t read_id, const float *e
             // n = 2 keeps the band rule from treating the piece as one row
             if (band_for(2, sc.m, cd.band_w, cd.slope_num, cd.slope_den, sc.band, sc.w_report) != 0)
                 return RA_EINVAL;
+            if (sc.band.num > 0)  // lets band_cells count a chunk in O(1) away from the table's edges
+                sc.band.per = sc.band.den / std::gcd(sc.band.num, sc.band.den);
             sc.fr_cap = (uint32_t)std::min<int64_t>(2 * sc.band.w + 2, (int64_t)sc.m + 1);
             sc.sig.ref_off = cd.ref_offset;
             sc.sig.len = cd.ref_len_bases;
@@ -487,31 +495,56 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     reap_done(h, st);
     if (st->pending.empty())
         return RA_OK;
-    // plan: one piece of work per (chunk, candidate)
-    std::vector<float> ev;
-    std::vector<SigDesc> sig;
-    std::vector<PlanItem> items;
-    std::vector<int> read_of;
+    const auto t_plan = std::chrono::steady_clock::now();
+    // plan: one piece of work per (chunk, candidate).  A first serial pass
+    // places every chunk's events, pieces and signal descriptors (prefix
+    // sums) and registers its tickets; the second fills the records on the
+    // host worker threads.  Each read has at most one pending chunk, so the
+    // chunks touch disjoint read state; only the handle-wide shape cache is
+    // shared (under a lock).
     FlushRec *f = new FlushRec();
     struct Update {  // host state advanced only once the flush is launched
         ServeCand *sc;
         int32_t fr_lo, fr_wid;
         bool dead;
     };
-    std::vector<Update> updates;
-    uint32_t chunk_idx = 0;
-    for (auto &pc : st->pending) {
-        ServeRead &rd = st->reads[pc.read_id];
+    const size_t n_pend = st->pending.size();
+    std::vector<ServeRead *> rds(n_pend);
+    std::vector<uint64_t> ev_first(n_pend + 1, 0), item_first(n_pend + 1, 0), sig_first(n_pend + 1, 0);
+    for (size_t ci = 0; ci < n_pend; ++ci) {
+        const PendingChunk &pc = st->pending[ci];
+        ServeRead &rd = st->reads.at(pc.read_id);
+        rds[ci] = &rd;
+        const uint64_t nrows = pc.ev.size();
+        const uint64_t count = nrows ? rd.cands.size() : 0;  // a close-only chunk returns nothing
+        ev_first[ci + 1] = ev_first[ci] + nrows;
+        item_first[ci + 1] = item_first[ci] + count;
+        sig_first[ci + 1] = sig_first[ci] + (rd.signal_done ? 0 : count);
+        for (uint64_t t : pc.tickets)
+            f->tickets.push_back({t, pc.read_id, (uint32_t)item_first[ci], (uint32_t)count, pc.last});
+        if (pc.last)
+            f->closing.push_back(pc.read_id);
+    }
+    const uint32_t chunk_idx = (uint32_t)n_pend;
+    std::vector<float> ev(ev_first[n_pend]);
+    std::vector<SigDesc> sig(sig_first[n_pend]);
+    std::vector<PlanItem> items(item_first[n_pend]);
+    std::vector<int> read_of(item_first[n_pend]);
+    std::vector<Update> updates(item_first[n_pend]);
+    auto plan_chunk = [&](size_t ci) {
+        const PendingChunk &pc = st->pending[ci];
+        ServeRead &rd = *rds[ci];
         const uint32_t row0 = rd.rows_done, nrows = (uint32_t)pc.ev.size();
-        const uint64_t ev_off = ev.size();
-        ev.insert(ev.end(), pc.ev.begin(), pc.ev.end());
-        const uint32_t first = (uint32_t)items.size();
-        const uint32_t count = nrows ? (uint32_t)rd.cands.size() : 0;  // a close-only chunk returns nothing
+        const uint64_t ev_off = ev_first[ci];
+        if (nrows)
+            memcpy(ev.data() + ev_off, pc.ev.data(), sizeof(float) * nrows);
+        const uint32_t first = (uint32_t)item_first[ci];
+        const uint32_t count = (uint32_t)(item_first[ci + 1] - first);
         for (uint32_t c = 0; c < count; ++c) {
             ServeCand &sc = rd.cands[c];
             if (!rd.signal_done)
-                sig.push_back(sc.sig);
-            PlanItem it;
+                sig[sig_first[ci] + c] = sc.sig;
+            PlanItem &it = items[first + c];
             memset(&it.wd, 0, sizeof(WorkDesc));
             WorkDesc &wd = it.wd;
             wd.ev_off = ev_off;
@@ -522,8 +555,8 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
             wd.nrows = (int32_t)nrows;
             wd.m = (int32_t)sc.m;
             wd.w = (int32_t)sc.band.w;
-            wd.cand = (int32_t)items.size();
-            wd.read = (int32_t)chunk_idx;
+            wd.cand = (int32_t)(first + c);
+            wd.read = (int32_t)ci;
             wd.n_read = (int32_t)(row0 + nrows);
             wd.w_report = sc.w_report;
             if (row0 == 0) {
@@ -553,14 +586,23 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
                 // candidates of one shape (chunk height, band, table width)
                 // share one choice across reads: a small handle-wide cache
                 const ShapeKey key{(int64_t)nrows, sc.band.num, sc.band.den, sc.band.w, sc.band.m};
-                auto hit = st->shape_variant.find(key);
-                if (hit != st->shape_variant.end()) {
-                    it.variant = hit->second;
+                int cached = -1;
+                {
+                    std::lock_guard<std::mutex> lk(st->shape_mu);
+                    auto hit = st->shape_variant.find(key);
+                    if (hit != st->shape_variant.end())
+                        cached = hit->second;
+                }
+                if (cached >= 0) {
+                    it.variant = cached;
                     sch = schedule(sc.band, row0, nrows, kVariants[it.variant][0], kVariants[it.variant][1]);
                 } else {
                     it.variant = choose_variant(sc.band, row0, nrows, sch, h->slot_cost);
-                    if (sch.s_end > 0 && st->shape_variant.size() < 4096)
-                        st->shape_variant[key] = it.variant;
+                    if (sch.s_end > 0) {
+                        std::lock_guard<std::mutex> lk(st->shape_mu);
+                        if (st->shape_variant.size() < 4096)
+                            st->shape_variant[key] = it.variant;
+                    }
                 }
                 if (sch.s_end <= 0) {
                     it.variant = 0;
@@ -572,10 +614,10 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
             wd.dC = sch.dC;
             wd.a0 = sch.a0;
             wd.s_end = sch.s_end;
+            wd.cells = sch.s_end > 0 ? band_cells(sc.band, row0, (int64_t)row0 + nrows) : 0;
             it.cost = (double)sch.s_end * kVariants[it.variant][0];
             it.cap = ring_need(wd, kVariants[it.variant][0], h->plan.ring_bin_shift);
-            items.push_back(it);
-            read_of.push_back((int)chunk_idx);
+            read_of[first + c] = (int)ci;
             // the band of this piece's last row is the row above the next piece
             Update u{&sc, sc.fr_lo, sc.fr_wid, sc.dead};
             if (!sc.dead) {
@@ -587,13 +629,16 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
                     u.dead = true;
                 }
             }
-            updates.push_back(u);
+            updates[first + c] = u;
         }
-        for (uint64_t t : pc.tickets)
-            f->tickets.push_back({t, pc.read_id, first, count, pc.last});
-        if (pc.last)
-            f->closing.push_back(pc.read_id);
-        chunk_idx++;
+    };
+    {
+        // about 64 chunks (some thousand pieces) per host thread at least
+        const unsigned T = (unsigned)std::min<size_t>(host_threads(), std::max<size_t>(1, n_pend / 64));
+        run_tasks(T, [&](unsigned t) {
+            for (size_t ci = n_pend * t / T; ci < n_pend * (t + 1) / T; ++ci)
+                plan_chunk(ci);
+        });
     }
     const uint32_t n_items = (uint32_t)items.size();
     if (n_items == 0) {
@@ -666,6 +711,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     memset(hin + o_keys, 0, in_bytes - o_keys);
     cudaStream_t s = h->stream;
     const auto t_launch = std::chrono::steady_clock::now();
+    st->stats.host_plan_ms += std::chrono::duration<double, std::milli>(t_launch - t_plan).count();
     // timing events (start, inputs copied, kernels done, done), reused
     while (st->timing_events.size() < 4) {
         cudaEvent_t e = nullptr;

@@ -25,10 +25,14 @@
 // min -> add chain.  The rows in band at column j form an interval, found
 // each step by a column-wise DDA (the last row whose band reaches j; the
 // first row whose band has started is that one less a constant) and turned
-// into a bit mask by one bmsk instruction.  The population count of the
-// mask is the lane's in-band cells of the step, so the stripe change, which
-// each lane makes alone while the rest of its warp waits, only loads the
-// lane's events and finds its last column in O(1).
+// into a bit mask by one bmsk instruction.  Rows past the piece's last row
+// hold event +inf, so the mask need not be clipped to them.  The host counts
+// each piece's in-band cells exactly (a floor sum over its rows) and the
+// kernel copies that count into the result; only the early-terminating
+// instantiation, which may stop inside the band, counts the cells it computes
+// (the population count of each step's mask).  The stripe change, which each
+// lane makes alone while the rest of its warp waits, loads the lane's events
+// and finds its last column in O(1).
 // The cell itself is sub, min3 (one exact 3-input min), add, in that order.
 #pragma once
 
@@ -45,7 +49,7 @@ namespace ra {
 struct GroupCold {
     const float *ev;
     uint64_t fout_off;
-    int nrows, row0, K, dC, den, q1, r1, qH, rH, t_last, r_last, cand, read, n_read, w_rep, fout_lo;
+    int nrows, row0, K, dC, den, q1, r1, qH, rH, qR, rR, t_last, r_last, cand, read, n_read, w_rep, fout_lo;
     int qdC, rdC, s_end, abort, written;  // abort/written: early termination
     float lb;                              // early termination: cost lower bound at the abort
 };
@@ -128,15 +132,27 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         const int loQ = lc->loQ, loR = lc->loR, hiQ = lc->hiQ, hiR = lc->hiR;
         b = -1;
         nvalid = min(max(nrows - i0, 0), HR);
+        // rows past the last one get event +inf, so they stay +inf whatever
+        // the band mask says
+        const float *evp = ev + i0;
+        if (nvalid == HR) {
 #pragma unroll
-        for (int r = 0; r < HR; ++r) {
-            const int li = i0 + r;
-            if (li < nrows)
-                e[r] = __ldg(ev + li);
+            for (int r = 0; r < HR; ++r)
+                e[r] = __ldg(evp + r);
+        } else {
+#pragma unroll
+            for (int r = 0; r < HR; ++r)
+                e[r] = (r < nvalid) ? __ldg(evp + r) : kInf;
         }
         // the lane leaves the stripe after the band end of its last row
-        // (clamped to the table); its in-band cells are counted per step
-        if (nvalid > 0) {
+        // (clamped to the table); a full stripe's last row is HR - 1 rows
+        // below the first, a step of (qR, rR) precomputed per alignment
+        if (nvalid == HR) {
+            int Qh = hiQ + gc->qR, Rh = hiR + gc->rR;
+            if (Rh >= den)
+                Qh += 1;
+            b = Qh < m - 1 ? Qh : m - 1;
+        } else if (nvalid > 0) {
             int Qh, Rh;
             row_dda(hiQ, hiR, q1, r1, den, nvalid - 1, Qh, Rh);
             b = Qh < m - 1 ? Qh : m - 1;
@@ -194,12 +210,16 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
     auto band_mask = [&]() -> unsigned {
         const int Aq = Bq - Dq - (Br < Dr ? 1 : 0);
         const int loN = max(Aq, 0);
-        const int hiN = min(Bq + 1, nvalid);
+        // rows past the last one are +inf through their events; only the
+        // early-terminating kernel, which counts the cells it computes,
+        // clips the mask to them
+        const int hiN = ET ? min(Bq + 1, nvalid) : Bq + 1;
         const int width = max(hiN - loN, 0);
         unsigned M;
         asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(M) : "r"(loN), "r"(width));
         M = ((unsigned)j <= (unsigned)colmax) ? M : 0u;
-        ncells += __popc(M);
+        if (ET)
+            ncells += __popc(M);
         return M;
     };
     auto dda_step = [&]() {
@@ -410,13 +430,16 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
     while (true) {
         const bool need = done && !exhausted;
         if (__any_sync(FULL, need)) {
-            // finished groups: add up the in-band cells of their lanes
-            unsigned long long c = lc->cells;
+            if (ET) {
+                // finished groups: add up the in-band cells their lanes
+                // computed (a pruned alignment stops short of its band)
+                unsigned long long c = lc->cells;
 #pragma unroll
-            for (int off = 1; off < G; off <<= 1)
-                c += __shfl_xor_sync(FULL, c, off);
-            if (need && have && t == 0)
-                p.results[gc->cand].cells = c;
+                for (int off = 1; off < G; off <<= 1)
+                    c += __shfl_xor_sync(FULL, c, off);
+                if (need && have && t == 0)
+                    p.results[gc->cand].cells = c;
+            }
             if (need)
                 have = false;
             int tk = 0;
@@ -488,6 +511,10 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
                             gc->r1 = (int)(num % dn);
                             gc->qH = (int)(Hn / dn);
                             gc->rH = (int)(Hn % dn);
+                            gc->qR = (int)((HR - 1) * num / dn);
+                            gc->rR = (int)((HR - 1) * num % dn);
+                            if (!ET)
+                                p.results[wd.cand].cells = wd.cells;
                             gc->t_last = nl / HR;
                             gc->r_last = nl % HR;
                             gc->cand = wd.cand;
@@ -620,8 +647,10 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
             }
         }
         s += nstep;
-        lc->cells += ncells;
-        ncells = 0;
+        if (ET) {
+            lc->cells += ncells;
+            ncells = 0;
+        }
         if (!done && s == s_end)
             done = true;
         if (ET) {

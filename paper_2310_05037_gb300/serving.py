@@ -234,7 +234,8 @@ class ServingLoop:
         st.host = {"python_submit": t_sub * 1e3, "python_flush": t_flush * 1e3, "python_poll_wait": t_poll * 1e3,
                    "python_other": (st.wall_s - t_sub - t_flush - t_poll) * 1e3,
                    "library_submit": lib.host_submit_ms, "library_flush_plan_launch": lib.host_flush_ms,
-                   "library_flush_cuda_calls": lib.host_launch_ms,
+                   "library_flush_cuda_calls": lib.host_launch_ms, "library_flush_planning": lib.host_plan_ms,
+                   "library_reap": lib.host_reap_ms,
                    "device_h2d": lib.h2d_ms, "device_kernels": lib.device_ms, "device_d2h": lib.d2h_ms,
                    "flushes": float(lib.flushes)}
         return st

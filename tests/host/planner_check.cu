@@ -21,6 +21,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
+#include <numeric>
 #include <random>
 #include <thread>
 #include <vector>
@@ -252,6 +253,47 @@ int main()
                 CHECK(cls[ci - 1].max_cost >= cl.max_cost, "classes not longest first\n");
         }
         CHECK(covered == items.size(), "classes do not cover the items\n");
+    }
+    // the exact in-band cell count the striped kernel reports (floor sums,
+    // and the O(1) form away from the table's edges) against row-by-row sums
+    {
+        uint64_t cell_cases = 0;
+        for (int rep = 0; rep < 60000; ++rep) {
+            BandDef b;
+            const int64_t n = 1 + (int64_t)(rng() % 3000);
+            b.m = 1 + (int64_t)(rng() % 4000);
+            if (rng() % 5 == 0) {
+                b.num = 0;
+                b.den = 1;
+                b.w = (rng() % 2) ? b.m : 1 + (int64_t)(rng() % 50);
+            } else {
+                b.num = 1 + (int64_t)(rng() % 3000);
+                b.den = 1 + (int64_t)(rng() % 3000);
+                b.w = 1 + (int64_t)(rng() % 80);
+                if (rng() % 2)
+                    b.per = b.den / std::gcd(b.num, b.den);
+            }
+            if (rep % 1000 == 0) {  // slopes and widths at the planner's limits
+                b.num = 1 + (int64_t)(rng() % (1ll << 30));
+                b.den = 1 + (int64_t)(rng() % (1ll << 30));
+                b.w = 1 + (int64_t)(rng() % 5000);
+                b.m = 1 + (int64_t)(rng() % 200000);
+                b.per = 0;
+            }
+            const int64_t r0 = (int64_t)(rng() % (n + 1)), r1 = r0 + (int64_t)(rng() % 400);
+            uint64_t brute = 0;
+            for (int64_t i = r0; i < r1; ++i) {
+                const int64_t c = b.hi(i) - b.lo(i) + 1;
+                if (c > 0)
+                    brute += (uint64_t)c;
+            }
+            const uint64_t got = band_cells(b, r0, r1);
+            CHECK(got == brute, "band_cells num %lld den %lld w %lld m %lld rows %lld..%lld: %llu, rows say %llu\n",
+                  (long long)b.num, (long long)b.den, (long long)b.w, (long long)b.m, (long long)r0, (long long)r1,
+                  (unsigned long long)got, (unsigned long long)brute);
+            ++cell_cases;
+        }
+        cases += cell_cases;
     }
     printf("cases %llu steps %llu fails %d\n", (unsigned long long)cases, (unsigned long long)steps, fails);
     return fails ? 1 : 0;

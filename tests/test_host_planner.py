@@ -2,8 +2,9 @@
 against the library's planning header and runs it.  It replays the striped
 kernel's lane schedule for random bands and every variant and verifies the
 period, ring size and step count the planner computes in closed form, the
-launch-class ordering, the kernel's O(1) row step of the band DDA, and the
-host worker pool's parallel loops."""
+launch-class ordering, the kernel's O(1) row step of the band DDA, the exact
+in-band cell count the kernel reports (floor sums) against row-by-row sums,
+and the host worker pool's parallel loops."""
 import os
 import shutil
 import subprocess
