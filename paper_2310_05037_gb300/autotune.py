@@ -102,26 +102,25 @@ def tune_plan(workload, costs=None, device="cuda:0", runs=3, ring_bins=(2, 1), l
     times = {}
     with tempfile.TemporaryDirectory() as d:
         for rb, ls, bs in [(rb, ls, bs) for rb in ring_bins for ls in latency_splits for bs in block_splits]:
-            if True:
-                path = os.path.join(d, "t_%d_%g_%s.txt" % (rb, ls, bs))
-                knobs = {"ring_bins": rb, "latency_split": ls}
-                if bs is not None:
-                    knobs["block_split"] = bs
-                write_table(path, costs or {}, knobs)
-                al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena_bytes, k=w.k, device=device,
-                               autotune_path=path)
-                try:
-                    b = al.prepare(w.events, w.read_offsets, w.cands)
+            path = os.path.join(d, "t_%d_%g_%s.txt" % (rb, ls, bs))
+            knobs = {"ring_bins": rb, "latency_split": ls}
+            if bs is not None:
+                knobs["block_split"] = bs
+            write_table(path, costs or {}, knobs)
+            al = B.Aligner(w.pore, w.ref2bit, w.ref_len, arena_bytes=arena_bytes, k=w.k, device=device,
+                           autotune_path=path)
+            try:
+                b = al.prepare(w.events, w.read_offsets, w.cands)
+                al.poll(al.run(b), 0)
+                best = None
+                for _ in range(runs):
                     al.poll(al.run(b), 0)
-                    best = None
-                    for _ in range(runs):
-                        al.poll(al.run(b), 0)
-                        ms = al.stats(b).dtw_ms
-                        best = ms if best is None else min(best, ms)
-                    times[(rb, ls) if bs is None else (rb, ls, bs)] = best
-                    al.release(b)
-                finally:
-                    al.close()
+                    ms = al.stats(b).dtw_ms
+                    best = ms if best is None else min(best, ms)
+                times[(rb, ls) if bs is None else (rb, ls, bs)] = best
+                al.release(b)
+            finally:
+                al.close()
     best = min(times, key=times.get)
     plan = {"ring_bins": best[0], "latency_split": best[1]}
     if len(best) > 2:

@@ -14,6 +14,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -177,7 +178,8 @@ inline int64_t cdiv(int64_t a, int64_t b) { return -fdiv(-a, b); }
 
 struct BandDef {
     int64_t num = 0, den = 1, w = 0, m = 1;
-    int64_t per = 0;  // den / gcd(num, den) when known (0: not computed), see band_cells
+    int64_t per = 0;    // den / gcd(num, den) when known (0: not computed), see band_cells
+    int64_t hi_row = 0; // with per: the first row whose band reaches the last column
     int64_t lo(int64_t i) const { return std::max<int64_t>(0, cdiv(i * num - w * den, den)); }
     int64_t hi(int64_t i) const { return std::min<int64_t>(m - 1, fdiv(i * num + w * den, den)); }
 };
@@ -217,6 +219,22 @@ inline uint64_t floor_sum(uint64_t n, uint64_t c, uint64_t a, uint64_t b)
     return (uint64_t)acc;
 }
 
+// Fills a band's per and hi_row, which let band_cells count rows away from
+// the table's edges in O(1) (for bands counted many times, as in serving).
+inline void prepare_cell_count(BandDef &b)
+{
+    if (b.num <= 0)
+        return;
+    int64_t x = b.num, y = b.den;
+    while (y) {
+        const int64_t t = x % y;
+        x = y;
+        y = t;
+    }
+    b.per = b.den / x;
+    b.hi_row = std::max<int64_t>(0, cdiv((b.m - 1 - b.w) * b.den, b.num));
+}
+
 // In-band cells of rows [r0, r1) of a band (the table's cells (i, j) with
 // lo(i) <= j <= hi(i)), exactly, in O(log den): the sums of hi and of lo over
 // the rows are floor sums between the rows where the band meets the table's
@@ -232,15 +250,15 @@ inline uint64_t band_cells(const BandDef &b, int64_t r0, int64_t r1)
     if (r1 <= r0)
         return 0;
     const uint64_t num = (uint64_t)b.num, den = (uint64_t)b.den, wd = (uint64_t)(b.w * b.den);
-    // sum of hi: floor((i num + w den) / den) below i_h, m - 1 from i_h on
-    const int64_t i_h = std::max<int64_t>(0, cdiv((b.m - 1 - b.w) * b.den, b.num));
-    if (b.per > 0 && r1 <= i_h && r0 * b.num >= b.w * b.den - b.den + 1) {
+    if (b.per > 0 && r1 <= b.hi_row && r0 * b.num >= b.w * b.den - b.den + 1) {
         // no row of the range meets an edge of the table: with x = i num / den,
         // hi - lo + 1 = floor(x + w) - ceil(x - w) + 1 = 2w + [x is whole],
         // and x is whole exactly on the multiples of den / gcd(num, den)
         const uint64_t whole = (uint64_t)(fdiv(r1 - 1, b.per) - fdiv(r0 - 1, b.per));
         return (uint64_t)(r1 - r0) * (uint64_t)(2 * b.w) + whole;
     }
+    // sum of hi: floor((i num + w den) / den) below i_h, m - 1 from i_h on
+    const int64_t i_h = std::max<int64_t>(0, cdiv((b.m - 1 - b.w) * b.den, b.num));
     uint64_t s_hi = 0;
     {
         const int64_t a = r0, e = std::min(r1, std::max(r0, i_h));
@@ -338,35 +356,131 @@ inline Sched schedule(const BandDef &b, int64_t row0, int64_t nrows, int G, int 
     return s;
 }
 
+// The schedule of consecutive chunks of one candidate (serving): pieces of
+// `rows` rows starting at row0, row0 + rows, ... with one variant.  Instead
+// of the divisions of schedule() and the band edges per chunk, it keeps the
+// band's edge numerators at the next chunk's first row as quotient and
+// remainder by den, and steps them by precomputed increments.  The results
+// are the same as schedule(band, row0, rows, G, HR), band.lo and band.hi
+// (checked against them on the CPU).
+struct ChunkSched {
+    int64_t row0 = -1;               // first row of the next chunk (-1: not set up)
+    int64_t rows = 0;
+    int G = 0, HR = 0;
+    int64_t qx = 0, rx = 0;          // row0 * num - w * den = qx * den + rx, 0 <= rx < den
+    int64_t qy = 0, ry = 0;          // row0 * num + w * den = qy * den + ry
+    int64_t q1 = 0, r1 = 0;          // (rows - 1) * num = q1 * den + r1
+    int64_t qa = 0, ra = 0;          // rows * num
+    int64_t dC = 0, tail = 0;        // stripe period; kLag * t_last + (K - 1) * dC
+    int64_t rm = 0, qp = 0, rp = 0;  // with band.per: (row0 - 1) mod per, rows = qp * per + rp
+
+    void init(const BandDef &b, int64_t first_row, int64_t n, int g, int hr)
+    {
+        row0 = first_row;
+        rows = n;
+        G = g;
+        HR = hr;
+        const int64_t X = first_row * b.num - b.w * b.den, Y = first_row * b.num + b.w * b.den;
+        qx = fdiv(X, b.den);
+        rx = X - qx * b.den;
+        qy = fdiv(Y, b.den);
+        ry = Y - qy * b.den;
+        q1 = (n - 1) * b.num / b.den;
+        r1 = (n - 1) * b.num - q1 * b.den;
+        qa = n * b.num / b.den;
+        ra = n * b.num - qa * b.den;
+        const int64_t H = (int64_t)g * hr, K = (n + H - 1) / H;
+        int64_t span = fdiv(2 * b.w * b.den - (H - hr + 1) * b.num, b.den);
+        span = std::min<int64_t>(span, b.m - 1);
+        dC = std::max<int64_t>((int64_t)kLag * g + 3, span + 2);
+        tail = (int64_t)kLag * ((n - 1 - (K - 1) * H) / hr) + (K - 1) * dC;
+        if (b.per > 0) {
+            rm = (first_row - 1) - fdiv(first_row - 1, b.per) * b.per;
+            qp = n / b.per;
+            rp = n - qp * b.per;
+        }
+    }
+    // the chunk starting at row0: its schedule and the band of its last row
+    // (lo_last, hi_last, clipped to the table), then steps to the next chunk
+    void next(const BandDef &b, Sched &s, int64_t &lo_last, int64_t &hi_last, uint64_t &cells)
+    {
+        // in-band cells: away from the table's edges 2w per row plus the rows
+        // where row num / den is whole (the multiples of per, counted from
+        // the running remainder), else the floor sums
+        if (b.per > 0 && row0 + rows <= b.hi_row && row0 * b.num >= b.w * b.den - b.den + 1)
+            cells = (uint64_t)rows * (uint64_t)(2 * b.w) + (uint64_t)(qp + (rm + rp >= b.per ? 1 : 0));
+        else
+            cells = band_cells(b, row0, row0 + rows);
+        if (b.per > 0) {
+            rm += rp;
+            if (rm >= b.per)
+                rm -= b.per;
+        }
+        s = Sched();
+        const int64_t a0 = std::max<int64_t>(0, qx + (rx > 0 ? 1 : 0));
+        int64_t lx = qx + q1, lrx = rx + r1;
+        if (lrx >= b.den) {
+            lx += 1;
+            lrx -= b.den;
+        }
+        int64_t ly = qy + q1, lry = ry + r1;
+        if (lry >= b.den)
+            ly += 1;
+        lo_last = std::max<int64_t>(0, lx + (lrx > 0 ? 1 : 0));
+        hi_last = std::min<int64_t>(b.m - 1, ly);
+        s.a0 = (int32_t)a0;
+        if (a0 <= b.m - 1) {
+            s.dC = (int32_t)dC;
+            s.s_end = (int32_t)std::max<int64_t>(hi_last - a0 + 3 + tail, 1);
+        }
+        row0 += rows;
+        qx += qa;
+        rx += ra;
+        if (rx >= b.den) {
+            qx += 1;
+            rx -= b.den;
+        }
+        qy += qa;
+        ry += ra;
+        if (ry >= b.den) {
+            qy += 1;
+            ry -= b.den;
+        }
+    }
+};
+
 // ---------------------------------------------------------------- arena
+// Best-fit allocator over the caller's arena: free ranges indexed by offset
+// (to merge a released range with its neighbours) and by size (to find the
+// smallest range that fits in O(log n)); 256-byte granules.
 struct Arena {
     char *base = nullptr;
     uint64_t size = 0;
-    std::map<uint64_t, uint64_t> free_;  // offset -> size
     void init(void *p, uint64_t n)
     {
         base = (char *)p;
         size = n;
         free_.clear();
+        by_size_.clear();
+        used_.clear();
         if (n)
-            free_[0] = n;
+            add_free(0, n);
     }
     void *alloc(uint64_t n)
     {
         n = (n + 255) & ~255ull;
         if (n == 0)
             n = 256;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= n) {
-                uint64_t off = it->first, sz = it->second;
-                free_.erase(it);
-                if (sz > n)
-                    free_[off + n] = sz - n;
-                used_[off] = n;
-                return base + off;
-            }
-        }
-        return nullptr;
+        auto bs = by_size_.lower_bound(std::make_pair(n, (uint64_t)0));
+        if (bs == by_size_.end())
+            return nullptr;
+        const uint64_t off = bs->second, sz = bs->first;
+        by_size_.erase(bs);
+        free_.erase(off);
+        if (sz > n)
+            add_free(off + n, sz - n);
+        used_[off] = n;
+        return base + off;
     }
     void release(void *p)
     {
@@ -378,21 +492,34 @@ struct Arena {
             return;
         uint64_t n = u->second;
         used_.erase(u);
-        auto it = free_.emplace(off, n).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
+        // merge with the free neighbours on both sides
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && off + n == nx->first) {
+            n += nx->second;
+            by_size_.erase(std::make_pair(nx->second, nx->first));
+            nx = free_.erase(nx);
         }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
+        if (nx != free_.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                off = pv->first;
+                n += pv->second;
+                by_size_.erase(std::make_pair(pv->second, pv->first));
+                free_.erase(pv);
             }
         }
+        add_free(off, n);
     }
-    std::map<uint64_t, uint64_t> used_;
+
+private:
+    void add_free(uint64_t off, uint64_t n)
+    {
+        free_[off] = n;
+        by_size_.insert(std::make_pair(n, off));
+    }
+    std::map<uint64_t, uint64_t> free_;                 // offset -> size
+    std::set<std::pair<uint64_t, uint64_t>> by_size_;   // (size, offset)
+    std::map<uint64_t, uint64_t> used_;                 // offset -> size
 };
 
 struct ClassLaunch {

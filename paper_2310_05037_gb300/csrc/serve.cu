@@ -37,6 +37,7 @@ struct ServeCand {
     SigDesc sig{};
     int64_t plan_rows = -1; // chunk height of the cached variant choice
     int plan_variant = 0;   // variant chosen for chunks of plan_rows rows
+    ChunkSched csched;      // schedule of the next chunk of plan_rows rows, stepped without divisions
 };
 
 struct ServeRead {
@@ -122,11 +123,47 @@ struct ServeState {
     uint32_t max_events = 0;
     int max_cands = 0;
     int active = 0;
-    std::map<uint64_t, ServeRead> reads;
-    std::vector<PendingChunk> pending;
+    std::unordered_map<uint64_t, ServeRead> reads;
+    std::vector<PendingChunk> pending;  // [0, n_pending) are queued; later entries keep their buffers for reuse
+    size_t n_pending = 0;
     std::map<uint64_t, FlushRec *> flushes;       // by flush id
-    std::map<uint64_t, uint64_t> ticket_flush;    // ticket -> flush id
-    std::map<uint64_t, std::vector<rawalign_result_t>> ready;  // reaped results by ticket
+    std::unordered_map<uint64_t, uint64_t> ticket_flush;  // ticket -> flush id
+    // reaped results: one block per flush, and per ticket its place in the block
+    struct ReadyBlock {
+        std::vector<rawalign_result_t> res;
+        uint32_t left = 0;  // tickets not polled yet
+    };
+    struct ReadyRef {
+        uint64_t fid;
+        uint32_t first, count;
+    };
+    std::unordered_map<uint64_t, ReadyBlock> ready_blocks;  // by flush id
+    std::unordered_map<uint64_t, ReadyRef> ready;           // by ticket
+    std::vector<std::vector<rawalign_result_t>> res_pool;   // result buffers of polled blocks, for reuse
+    void drop_block(std::unordered_map<uint64_t, ReadyBlock>::iterator b)
+    {
+        if (res_pool.size() < 8)
+            res_pool.push_back(std::move(b->second.res));
+        ready_blocks.erase(b);
+    }
+    // a flush's planning arrays, kept across flushes (no allocation, no
+    // first-touch page faults once they have grown)
+    struct Update {  // host state advanced only once the flush is launched
+        ServeCand *sc;
+        int32_t fr_lo, fr_wid;
+        bool dead;
+    };
+    struct FlushScratch {
+        std::vector<ServeRead *> rds;
+        std::vector<uint64_t> ev_first, item_first, sig_first;
+        std::vector<SigDesc> sig;
+        std::vector<PlanItem> items;
+        std::vector<int> read_of;
+        std::vector<Update> updates;
+        std::vector<int> order;
+        std::vector<ClassLaunch> classes;
+        SortScratch sort;
+    } scratch;
     std::unordered_map<uint64_t, size_t> pending_at;           // read id -> index in pending
     uint64_t next_flush = 1;
     PinnedPool pinned;
@@ -146,6 +183,10 @@ ServeState *state(rawalign_dtw *h)
             h->serve->slots = h->cfg.serve_slots;
             h->serve->max_events = h->cfg.serve_max_events > 0 ? (uint32_t)h->cfg.serve_max_events : 0;
             h->serve->max_cands = h->cfg.max_candidates > 0 ? h->cfg.max_candidates : 64;
+            h->serve->reads.reserve(2 * (size_t)h->serve->slots);
+            h->serve->ready.reserve(4 * (size_t)h->serve->slots);
+            h->serve->ticket_flush.reserve(4 * (size_t)h->serve->slots);
+            h->serve->pending_at.reserve(2 * (size_t)h->serve->slots);
         }
     }
     return h->serve;
@@ -191,20 +232,33 @@ void reap(rawalign_dtw *h, ServeState *st, uint64_t fid, FlushRec *f)
 #else
     const bool failed = false;
 #endif
-    for (auto &t : f->tickets) {
-        std::vector<rawalign_result_t> v(f->h_res + t.first, f->h_res + t.first + t.count);
-        const bool dead = reject && !t.last && t.count && v[0].decision == RA_PENDING &&
-                          unreachable(v.data(), t.count, h->cfg.b_match, st->max_events, h->cfg.score_threshold);
-        for (uint32_t c = 0; c < t.count; ++c) {
-            v[c].read_id = t.read_id;
-            v[c].cand_idx = c;
-            if ((t.last || dead) && v[c].decision == RA_PENDING)
-                v[c].decision = RA_UNMAPPED;
-            if (failed)
-                v[c].status = RA_EDEVICE;
+    {
+        // the flush's results in one block; each ticket refers to its part
+        ServeState::ReadyBlock &blk = st->ready_blocks[fid];
+        if (!st->res_pool.empty()) {
+            blk.res = std::move(st->res_pool.back());
+            st->res_pool.pop_back();
         }
-        st->ready[t.ticket] = std::move(v);
-        st->ticket_flush.erase(t.ticket);
+        blk.res.assign(f->h_res, f->h_res + f->n_items);
+        blk.left = (uint32_t)f->tickets.size();
+        rawalign_result_t *res = blk.res.data();
+        for (auto &t : f->tickets) {
+            rawalign_result_t *v = res + t.first;
+            const bool dead = reject && !t.last && t.count && v[0].decision == RA_PENDING &&
+                              unreachable(v, t.count, h->cfg.b_match, st->max_events, h->cfg.score_threshold);
+            for (uint32_t c = 0; c < t.count; ++c) {
+                v[c].read_id = t.read_id;
+                v[c].cand_idx = c;
+                if ((t.last || dead) && v[c].decision == RA_PENDING)
+                    v[c].decision = RA_UNMAPPED;
+                if (failed)
+                    v[c].status = RA_EDEVICE;
+            }
+            st->ready[t.ticket] = ServeState::ReadyRef{fid, t.first, t.count};
+            st->ticket_flush.erase(t.ticket);
+        }
+        if (blk.left == 0)
+            st->drop_block(st->ready_blocks.find(fid));
     }
     if (f->t_ev[0]) {
         float a = 0, b = 0, c = 0;
@@ -271,6 +325,24 @@ void serve_destroy(rawalign_dtw *h)
     h->serve = nullptr;
 }
 
+// Copies up to cap results of a reaped ticket into out and forgets the
+// ticket (and its flush's block once every ticket of the flush is taken).
+uint32_t take_ready(ServeState *st, std::unordered_map<uint64_t, ServeState::ReadyRef>::iterator r,
+                    rawalign_result_t *out, uint32_t cap)
+{
+    const ServeState::ReadyRef ref = r->second;
+    st->ready.erase(r);
+    auto b = st->ready_blocks.find(ref.fid);
+    if (b == st->ready_blocks.end())
+        return 0;
+    const uint32_t n = std::min(cap, ref.count);
+    if (n)
+        memcpy(out, b->second.res.data() + ref.first, sizeof(rawalign_result_t) * n);
+    if (--b->second.left == 0)
+        st->drop_block(b);
+    return n;
+}
+
 int serve_poll(rawalign_dtw *h, uint64_t ticket, rawalign_result_t *out, uint32_t cap, uint32_t *n_out,
                int64_t timeout_us, bool *handled)
 {
@@ -283,8 +355,8 @@ int serve_poll(rawalign_dtw *h, uint64_t ticket, rawalign_result_t *out, uint32_
         auto tf = st->ticket_flush.find(ticket);
         if (tf == st->ticket_flush.end()) {
             // queued but not flushed yet?
-            for (auto &pc : st->pending)
-                for (uint64_t t : pc.tickets)
+            for (size_t ci = 0; ci < st->n_pending; ++ci)
+                for (uint64_t t : st->pending[ci].tickets)
                     if (t == ticket) {
                         *handled = true;
                         return RA_ENOTREADY;
@@ -315,11 +387,7 @@ int serve_poll(rawalign_dtw *h, uint64_t ticket, rawalign_result_t *out, uint32_
             return RA_EDEVICE;
     }
     *handled = true;
-    uint32_t n = std::min<uint32_t>(cap, (uint32_t)r->second.size());
-    if (n)
-        memcpy(out, r->second.data(), sizeof(rawalign_result_t) * n);
-    *n_out = n;
-    st->ready.erase(r);
+    *n_out = take_ready(st, r, out, cap);
     return RA_OK;
 }
 
@@ -344,6 +412,7 @@ int submit_one(rawalign_dtw *h, ServeState *st, uint64_t read_id, const float *e
         const int k = h->cfg.k;
         ServeRead rd;
         rd.read_id = read_id;
+        rd.cands.reserve(n_cands);
         uint64_t floats = 0;
         for (uint32_t c = 0; c < n_cands; ++c) {
             const rawalign_candidate_t &cd = cands[c];
@@ -358,8 +427,7 @@ int submit_one(rawalign_dtw *h, ServeState *st, uint64_t read_id, const float *e
             // n = 2 keeps the band rule from treating the piece as one row
             if (band_for(2, sc.m, cd.band_w, cd.slope_num, cd.slope_den, sc.band, sc.w_report) != 0)
                 return RA_EINVAL;
-            if (sc.band.num > 0)  // lets band_cells count a chunk in O(1) away from the table's edges
-                sc.band.per = sc.band.den / std::gcd(sc.band.num, sc.band.den);
+            prepare_cell_count(sc.band);  // band_cells counts a chunk in O(1) away from the table's edges
             sc.fr_cap = (uint32_t)std::min<int64_t>(2 * sc.band.w + 2, (int64_t)sc.m + 1);
             sc.sig.ref_off = cd.ref_offset;
             sc.sig.len = cd.ref_len_bases;
@@ -403,9 +471,13 @@ int submit_one(rawalign_dtw *h, ServeState *st, uint64_t read_id, const float *e
     if (st->max_events && rd.rows_done + queued + n_events > st->max_events)
         return RA_EINVAL;
     if (!pc) {
-        st->pending_at[read_id] = st->pending.size();
-        st->pending.push_back(PendingChunk());
-        pc = &st->pending.back();
+        if (st->n_pending == st->pending.size())
+            st->pending.push_back(PendingChunk());
+        pc = &st->pending[st->n_pending];
+        st->pending_at[read_id] = st->n_pending++;
+        pc->ev.clear();
+        pc->tickets.clear();
+        pc->last = 0;
         pc->read_id = read_id;
     }
     pc->ev.insert(pc->ev.end(), events, events + n_events);
@@ -493,24 +565,25 @@ namespace {
 int flush_impl(rawalign_dtw *h, ServeState *st)
 {
     reap_done(h, st);
-    if (st->pending.empty())
+    if (st->n_pending == 0)
         return RA_OK;
     const auto t_plan = std::chrono::steady_clock::now();
-    // plan: one piece of work per (chunk, candidate).  A first serial pass
-    // places every chunk's events, pieces and signal descriptors (prefix
-    // sums) and registers its tickets; the second fills the records on the
-    // host worker threads.  Each read has at most one pending chunk, so the
-    // chunks touch disjoint read state; only the handle-wide shape cache is
-    // shared (under a lock).
+    // plan: one piece of work per (chunk, candidate).  A first pass places
+    // every chunk's events, pieces and signal descriptors (prefix sums) and
+    // registers its tickets; the second fills the records (on the host
+    // worker threads when the flush is large).  Each read has at most one
+    // pending chunk, so the chunks touch disjoint read state; only the
+    // handle-wide shape cache is shared (under a lock).
     FlushRec *f = new FlushRec();
-    struct Update {  // host state advanced only once the flush is launched
-        ServeCand *sc;
-        int32_t fr_lo, fr_wid;
-        bool dead;
-    };
-    const size_t n_pend = st->pending.size();
-    std::vector<ServeRead *> rds(n_pend);
-    std::vector<uint64_t> ev_first(n_pend + 1, 0), item_first(n_pend + 1, 0), sig_first(n_pend + 1, 0);
+    using Update = ServeState::Update;
+    ServeState::FlushScratch &sc_ = st->scratch;
+    const size_t n_pend = st->n_pending;
+    std::vector<ServeRead *> &rds = sc_.rds;
+    std::vector<uint64_t> &ev_first = sc_.ev_first, &item_first = sc_.item_first, &sig_first = sc_.sig_first;
+    rds.resize(n_pend);
+    ev_first.assign(n_pend + 1, 0);
+    item_first.assign(n_pend + 1, 0);
+    sig_first.assign(n_pend + 1, 0);
     for (size_t ci = 0; ci < n_pend; ++ci) {
         const PendingChunk &pc = st->pending[ci];
         ServeRead &rd = st->reads.at(pc.read_id);
@@ -526,18 +599,20 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
             f->closing.push_back(pc.read_id);
     }
     const uint32_t chunk_idx = (uint32_t)n_pend;
-    std::vector<float> ev(ev_first[n_pend]);
-    std::vector<SigDesc> sig(sig_first[n_pend]);
-    std::vector<PlanItem> items(item_first[n_pend]);
-    std::vector<int> read_of(item_first[n_pend]);
-    std::vector<Update> updates(item_first[n_pend]);
+    const uint64_t n_ev = ev_first[n_pend];
+    std::vector<SigDesc> &sig = sc_.sig;
+    std::vector<PlanItem> &items = sc_.items;
+    std::vector<int> &read_of = sc_.read_of;
+    std::vector<Update> &updates = sc_.updates;
+    sig.resize(sig_first[n_pend]);
+    items.resize(item_first[n_pend]);
+    read_of.resize(item_first[n_pend]);
+    updates.resize(item_first[n_pend]);
     auto plan_chunk = [&](size_t ci) {
         const PendingChunk &pc = st->pending[ci];
         ServeRead &rd = *rds[ci];
         const uint32_t row0 = rd.rows_done, nrows = (uint32_t)pc.ev.size();
         const uint64_t ev_off = ev_first[ci];
-        if (nrows)
-            memcpy(ev.data() + ev_off, pc.ev.data(), sizeof(float) * nrows);
         const uint32_t first = (uint32_t)item_first[ci];
         const uint32_t count = (uint32_t)(item_first[ci + 1] - first);
         for (uint32_t c = 0; c < count; ++c) {
@@ -546,6 +621,8 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
                 sig[sig_first[ci] + c] = sc.sig;
             PlanItem &it = items[first + c];
             memset(&it.wd, 0, sizeof(WorkDesc));
+            it.wave = 0;
+            it.split = false;
             WorkDesc &wd = it.wd;
             wd.ev_off = ev_off;
             wd.r_off = sc.r_off;
@@ -570,16 +647,22 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
             }
             wd.fout_off = sc.fr_off[1 - sc.cur];
             const int64_t last_row = (int64_t)row0 + nrows - 1;
-            wd.fout_lo = (int32_t)sc.band.lo(last_row);
+            int64_t lo_last = -1, hi_last = -1;  // band of the last row (computed below)
+            uint64_t cells = UINT64_MAX;          // in-band cells (computed below)
             Sched sch;
             if (sc.dead) {
                 it.variant = 0;
                 sch.s_end = 0;
             } else if (sc.plan_rows == (int64_t)nrows) {
                 // chunks of one height get one variant: the choice hardly
-                // depends on where the rows start (the results never do)
+                // depends on where the rows start (the results never do);
+                // their schedules follow from the previous chunk's
                 it.variant = sc.plan_variant;
-                sch = schedule(sc.band, row0, nrows, kVariants[it.variant][0], kVariants[it.variant][1]);
+                const int G = kVariants[it.variant][0], HR = kVariants[it.variant][1];
+                if (sc.csched.row0 != (int64_t)row0 || sc.csched.rows != (int64_t)nrows || sc.csched.G != G ||
+                    sc.csched.HR != HR)
+                    sc.csched.init(sc.band, row0, nrows, G, HR);
+                sc.csched.next(sc.band, sch, lo_last, hi_last, cells);
                 if (sch.s_end <= 0)
                     it.variant = 0;
             } else {
@@ -609,22 +692,32 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
                 } else {
                     sc.plan_rows = nrows;
                     sc.plan_variant = it.variant;
+                    sc.csched.init(sc.band, (int64_t)row0 + nrows, nrows, kVariants[it.variant][0],
+                                   kVariants[it.variant][1]);
                 }
             }
+            if (lo_last < 0) {
+                lo_last = sc.band.lo(last_row);
+                hi_last = sc.band.hi(last_row);
+            }
+            wd.fout_lo = (int32_t)lo_last;
             wd.dC = sch.dC;
             wd.a0 = sch.a0;
             wd.s_end = sch.s_end;
-            wd.cells = sch.s_end > 0 ? band_cells(sc.band, row0, (int64_t)row0 + nrows) : 0;
+            if (sch.s_end <= 0)
+                cells = 0;
+            else if (cells == UINT64_MAX)
+                cells = band_cells(sc.band, row0, (int64_t)row0 + nrows);
+            wd.cells = cells;
             it.cost = (double)sch.s_end * kVariants[it.variant][0];
             it.cap = ring_need(wd, kVariants[it.variant][0], h->plan.ring_bin_shift);
             read_of[first + c] = (int)ci;
             // the band of this piece's last row is the row above the next piece
             Update u{&sc, sc.fr_lo, sc.fr_wid, sc.dead};
             if (!sc.dead) {
-                const int64_t lo = sc.band.lo(last_row), hi = sc.band.hi(last_row);
-                if (hi >= lo && sch.s_end > 0) {
-                    u.fr_lo = (int32_t)lo;
-                    u.fr_wid = (int32_t)(hi - lo);
+                if (hi_last >= lo_last && sch.s_end > 0) {
+                    u.fr_lo = (int32_t)lo_last;
+                    u.fr_wid = (int32_t)(hi_last - lo_last);
                 } else {
                     u.dead = true;
                 }
@@ -633,8 +726,11 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         }
     };
     {
-        // about 64 chunks (some thousand pieces) per host thread at least
-        const unsigned T = (unsigned)std::min<size_t>(host_threads(), std::max<size_t>(1, n_pend / 64));
+        // one thread unless the flush is large: waking the worker threads
+        // costs more than planning a few thousand pieces (measured on GB300's
+        // host: 121 GCUPS served with one thread, 103 with sixteen)
+        const unsigned T = (unsigned)std::min<size_t>(
+            {(size_t)host_threads(), n_pend, std::max<size_t>(1, (size_t)item_first[n_pend] / 32768)});
         run_tasks(T, [&](unsigned t) {
             for (size_t ci = n_pend * t / T; ci < n_pend * (t + 1) / T; ++ci)
                 plan_chunk(ci);
@@ -650,13 +746,14 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         st->flushes[fid] = f;
         for (auto &t : f->tickets)
             st->ticket_flush[t.ticket] = fid;
-        st->pending.clear();
+        st->n_pending = 0;
         st->pending_at.clear();
         return RA_OK;
     }
-    std::vector<int> order;
-    std::vector<ClassLaunch> classes;
-    if (!make_classes(items, order, classes, /*longest_first=*/false)) {
+    std::vector<int> &order = sc_.order;
+    std::vector<ClassLaunch> &classes = sc_.classes;
+    classes.clear();
+    if (!make_classes(items.data(), items.size(), order, classes, sc_.sort, /*longest_first=*/false)) {
         delete f;
         return RA_EINVAL;
     }
@@ -671,7 +768,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     // events, signal descriptors, work records, read slots, and the zeroed
     // per-chunk best keys and queue counters
     auto al256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t b_ev = sizeof(float) * ev.size(), b_sig = sizeof(SigDesc) * sig.size();
+    const size_t b_ev = sizeof(float) * n_ev, b_sig = sizeof(SigDesc) * sig.size();
     const size_t b_work = sizeof(WorkDesc) * n_items, b_rd = sizeof(int) * n_items;
     const size_t b_keys = sizeof(unsigned long long) * chunk_idx, b_q = sizeof(int) * (kMaxClasses + 2);
     const size_t o_sig = al256(b_ev), o_work = o_sig + al256(b_sig), o_rd = o_work + al256(b_work);
@@ -702,11 +799,25 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     unsigned long long *d_keys = (unsigned long long *)(d_in + o_keys);
     int *d_queue = (int *)(d_in + o_q);
     char *hin = (char *)f->h_in;
-    memcpy(hin, ev.data(), b_ev);
+    {
+        // pack the pinned input block on the worker threads: each takes a
+        // range of chunks (their events) and a range of work records (in
+        // launch order)
+        WorkDesc *hw = (WorkDesc *)(hin + o_work);
+        float *hev = (float *)hin;
+        const unsigned T = (unsigned)std::min<size_t>(
+            {(size_t)host_threads(), n_pend, std::max<size_t>(1, (size_t)n_items / 32768)});
+        run_tasks(T, [&](unsigned t) {
+            for (size_t ci = n_pend * t / T; ci < n_pend * (t + 1) / T; ++ci) {
+                const PendingChunk &pc = st->pending[ci];
+                if (!pc.ev.empty())
+                    memcpy(hev + ev_first[ci], pc.ev.data(), sizeof(float) * pc.ev.size());
+            }
+            for (size_t x = (size_t)n_items * t / T; x < (size_t)n_items * (t + 1) / T; ++x)
+                hw[x] = items[order[x]].wd;
+        });
+    }
     memcpy(hin + o_sig, sig.data(), b_sig);
-    WorkDesc *hw = (WorkDesc *)(hin + o_work);
-    for (uint32_t x = 0; x < n_items; ++x)
-        hw[x] = items[order[x]].wd;
     memcpy(hin + o_rd, read_of.data(), b_rd);
     memset(hin + o_keys, 0, in_bytes - o_keys);
     cudaStream_t s = h->stream;
@@ -751,7 +862,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         p.b_match = h->cfg.b_match;
         p.end_free = 1;
         p.err = d_queue + kMaxClasses;
-        p.n_events = ev.size();
+        p.n_events = n_ev;
         p.n_r = h->arena.size / sizeof(float);
         p.n_fstore = h->arena.size / sizeof(float);
         p.n_results = (int)n_items;
@@ -777,10 +888,10 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         u.sc->fr_wid = u.fr_wid;
         u.sc->dead = u.dead;
     }
-    for (auto &pc : st->pending) {
-        ServeRead &rd = st->reads[pc.read_id];
+    for (size_t ci = 0; ci < n_pend; ++ci) {
+        ServeRead &rd = *rds[ci];
         rd.signal_done = true;
-        rd.rows_done += (uint32_t)pc.ev.size();
+        rd.rows_done += (uint32_t)st->pending[ci].ev.size();
     }
     st->stats.host_launch_ms += ms_since(t_launch);
     st->stats.flushes++;
@@ -790,7 +901,7 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     st->flushes[fid] = f;
     for (auto &t : f->tickets)
         st->ticket_flush[t.ticket] = fid;
-    st->pending.clear();
+    st->n_pending = 0;
     st->pending_at.clear();
     return RA_OK;
 }
@@ -807,12 +918,15 @@ extern "C" int rawalign_dtw_poll_chunks(rawalign_dtw_t *h, const uint64_t *ticke
         return RA_EINVAL;
     cudaSetDevice(h->device);
     // every ticket known and named once; the flushes still to wait for
-    std::unordered_set<uint64_t> seen;
+    {
+        std::vector<uint64_t> sorted(tickets, tickets + n_tickets);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+            return RA_EINVAL;
+    }
     std::vector<uint64_t> wait_for;
     for (uint32_t x = 0; x < n_tickets; ++x) {
         const uint64_t t = tickets[x];
-        if (!seen.insert(t).second)
-            return RA_EINVAL;
         if (st->ready.count(t))
             continue;
         auto tf = st->ticket_flush.find(t);
@@ -820,8 +934,8 @@ extern "C" int rawalign_dtw_poll_chunks(rawalign_dtw_t *h, const uint64_t *ticke
             wait_for.push_back(tf->second);
             continue;
         }
-        for (auto &pc : st->pending)
-            for (uint64_t q : pc.tickets)
+        for (size_t ci = 0; ci < st->n_pending; ++ci)
+            for (uint64_t q : st->pending[ci].tickets)
                 if (q == t)
                     return RA_ENOTREADY;  // queued, not flushed: waiting would not help
         return RA_EINVAL;
@@ -858,19 +972,15 @@ extern "C" int rawalign_dtw_poll_chunks(rawalign_dtw_t *h, const uint64_t *ticke
         auto r = st->ready.find(tickets[x]);
         if (r == st->ready.end())
             return RA_EDEVICE;
-        total += r->second.size();
+        total += r->second.count;
     }
     if (total > cap)
         return RA_EINVAL;
     uint64_t pos = 0;
     for (uint32_t x = 0; x < n_tickets; ++x) {
-        auto r = st->ready.find(tickets[x]);
-        const size_t n = r->second.size();
-        if (n)
-            memcpy(out + pos, r->second.data(), sizeof(rawalign_result_t) * n);
-        counts[x] = (uint32_t)n;
+        const uint32_t n = take_ready(st, st->ready.find(tickets[x]), out + pos, UINT32_MAX);
+        counts[x] = n;
         pos += n;
-        st->ready.erase(r);
     }
     return RA_OK;
 }

@@ -21,6 +21,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <numeric>
 #include <random>
 #include <thread>
@@ -271,7 +272,7 @@ int main()
                 b.den = 1 + (int64_t)(rng() % 3000);
                 b.w = 1 + (int64_t)(rng() % 80);
                 if (rng() % 2)
-                    b.per = b.den / std::gcd(b.num, b.den);
+                    prepare_cell_count(b);
             }
             if (rep % 1000 == 0) {  // slopes and widths at the planner's limits
                 b.num = 1 + (int64_t)(rng() % (1ll << 30));
@@ -294,6 +295,82 @@ int main()
             ++cell_cases;
         }
         cases += cell_cases;
+    }
+    // serving's incremental chunk schedule against schedule() and the band
+    // edges computed directly, over runs of consecutive chunks
+    {
+        for (int rep = 0; rep < 20000; ++rep) {
+            BandDef b;
+            b.m = 1 + (int64_t)(rng() % 6000);
+            b.num = 1 + (int64_t)(rng() % 3000);
+            b.den = 1 + (int64_t)(rng() % 3000);
+            b.w = 1 + (int64_t)(rng() % 200);
+            if (rep % 500 == 0) {
+                b.num = 1 + (int64_t)(rng() % (1ll << 30));
+                b.den = 1 + (int64_t)(rng() % (1ll << 30));
+            }
+            const int v = (int)(rng() % kNumVariants);
+            const int G = kVariants[v][0], HR = kVariants[v][1];
+            const int64_t rows = 1 + (int64_t)(rng() % 400);
+            int64_t row0 = (int64_t)(rng() % 3000);
+            if (rng() % 2)
+                prepare_cell_count(b);
+            ChunkSched cs;
+            cs.init(b, row0, rows, G, HR);
+            for (int c = 0; c < 30; ++c, row0 += rows) {
+                Sched got;
+                int64_t lo_last, hi_last;
+                uint64_t cells;
+                cs.next(b, got, lo_last, hi_last, cells);
+                CHECK(cells == band_cells(b, row0, row0 + rows), "chunk cells num %lld den %lld w %lld m %lld\n",
+                      (long long)b.num, (long long)b.den, (long long)b.w, (long long)b.m);
+                const Sched want = schedule(b, row0, rows, G, HR);
+                const int64_t last = row0 + rows - 1;
+                CHECK(got.a0 == want.a0 && got.s_end == want.s_end && got.dC == want.dC && lo_last == b.lo(last) &&
+                          hi_last == b.hi(last),
+                      "chunk schedule num %lld den %lld w %lld m %lld rows %lld row0 %lld G %d HR %d: "
+                      "a0 %d/%d s_end %d/%d dC %d/%d lo %lld/%lld hi %lld/%lld\n",
+                      (long long)b.num, (long long)b.den, (long long)b.w, (long long)b.m, (long long)rows,
+                      (long long)row0, G, HR, got.a0, want.a0, got.s_end, want.s_end, got.dC, want.dC,
+                      (long long)lo_last, (long long)b.lo(last), (long long)hi_last, (long long)b.hi(last));
+                ++cases;
+            }
+        }
+    }
+    // the arena allocator: live blocks never overlap and stay inside the
+    // arena; once everything is released the whole arena is one free range
+    {
+        const uint64_t kArena = 1ull << 24;
+        Arena ar;
+        ar.init((void *)0x10000, kArena);
+        std::map<uint64_t, uint64_t> live;  // offset -> bytes asked (rounded up to 256)
+        for (int op = 0; op < 200000; ++op) {
+            if (live.empty() || rng() % 3 != 0) {
+                const uint64_t n = 1 + rng() % (rng() % 8 == 0 ? 400000 : 5000);
+                void *p = ar.alloc(n);
+                if (!p)
+                    continue;
+                const uint64_t off = (uint64_t)((char *)p - (char *)0x10000), sz = (n + 255) & ~255ull;
+                CHECK(off % 256 == 0 && off + sz <= kArena, "arena block outside the arena\n");
+                auto nx = live.lower_bound(off);
+                if (nx != live.end())
+                    CHECK(off + sz <= nx->first, "arena blocks overlap\n");
+                if (nx != live.begin()) {
+                    auto pv = std::prev(nx);
+                    CHECK(pv->first + pv->second <= off, "arena blocks overlap\n");
+                }
+                live[off] = sz;
+            } else {
+                auto it = live.begin();
+                std::advance(it, (long)(rng() % live.size()));
+                ar.release((char *)0x10000 + it->first);
+                live.erase(it);
+            }
+            ++cases;
+        }
+        for (auto &kv : live)
+            ar.release((char *)0x10000 + kv.first);
+        CHECK(ar.alloc(kArena) != nullptr, "released arena does not merge back into one range\n");
     }
     printf("cases %llu steps %llu fails %d\n", (unsigned long long)cases, (unsigned long long)steps, fails);
     return fails ? 1 : 0;
