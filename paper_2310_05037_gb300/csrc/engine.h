@@ -203,12 +203,13 @@ inline uint64_t floor_sum(uint64_t n, uint64_t c, uint64_t a, uint64_t b)
         }
         // points (i, k) with k >= 1 and k c <= a i + b: per k, the rows
         // i >= (k c - b) / a; rewritten as a floor sum over k of (c k' + y % c) / a
-        if (a <= (UINT64_MAX - b) / n) {
-            const uint64_t y = a * n + b;
+        uint64_t an;
+        if (!__builtin_mul_overflow(a, n, &an) && an <= UINT64_MAX - b) {
+            const uint64_t y = an + b;
             if (y < c)
                 break;
             n = y / c;
-            b = y % c;
+            b = y - n * c;
         } else {
             const unsigned __int128 y = (unsigned __int128)a * n + b;
             n = (uint64_t)(y / c);
@@ -245,6 +246,10 @@ inline uint64_t band_cells(const BandDef &b, int64_t r0, int64_t r1)
         return 0;
     if (b.num == 0)
         return (uint64_t)(r1 - r0) * (uint64_t)(b.hi(0) - b.lo(0) + 1);
+    // a band that covers every row of the range whole (short pieces with a
+    // wide band, as most gaps of anchor-guided alignment): m cells per row
+    if (b.w >= b.m - 1 && r0 >= 0 && (r1 - 1) * b.num <= b.w * b.den)
+        return (uint64_t)(r1 - r0) * (uint64_t)b.m;
     // rows with lo(i) <= m - 1: i num - w den <= (m - 1) den
     r1 = std::min<int64_t>(r1, fdiv((b.m - 1 + b.w) * b.den, b.num) + 1);
     if (r1 <= r0)
