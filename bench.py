@@ -609,11 +609,33 @@ def run_reference(args, S):
         secs.append(cb["seconds"])
         samples.append(cb["sample"])
     value = statistics.mean(vals)
+    config = {"workload": workload_name(args), "reads": w.n_reads, "alignments": w.n_cands}
+    if w.anchor_offsets is None:
+        # the in-band cells of the whole workload: the oracle's band (slope
+        # num/den, half-width w_eff) gives each row the columns j with
+        # |j den - i num| <= w_eff den, clipped to the table
+        import oracle as O
+
+        lens = w.read_lengths()
+        rid = w.cands["read_id"].astype(np.int64)
+        total = 0
+        for c in range(w.n_cands):
+            n, m = int(lens[rid[c]]), int(w.cands["ref_len_bases"][c]) - w.k + 1
+            b = O.band_params(n, m, int(w.cands["band_w"][c]), int(w.cands["slope_num"][c]),
+                              int(w.cands["slope_den"][c]))
+            if b.unbanded:
+                total += n * m
+                continue
+            i = np.arange(n, dtype=np.int64)
+            lo = np.maximum(-((b.w_eff * b.den - i * b.num) // b.den), 0)
+            hi = np.minimum((i * b.num + b.w_eff * b.den) // b.den, m - 1)
+            total += int(np.maximum(hi - lo + 1, 0).sum())
+        config["cells_per_step"] = total
     out = {
         "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GCUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(secs), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(args), "reads": w.n_reads, "alignments": w.n_cands},
+        "config": config,
         "cpu_baseline": {**host_cpu(), "value": round(value, 5), "unit": "GCUPS", "cores": 1, "kind": "oracle",
                          "sample": "each step: random alignments of the workload for %.1f s, single thread; "
                                    "last: %s" % (per_step, samples[-1])},
