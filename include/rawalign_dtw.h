@@ -311,8 +311,9 @@ int rawalign_dtw_align_noalloc(const float *d_events, uint32_t n_events, const f
  * picks, per alignment, the variant with the fewest cost-weighted slots; the
  * autotuner measures these costs.  config.autotune_path may name a text file
  * of "G HR cost" lines with the same numbers, and the planner's bin edges:
- * "ring_bins S" (S = 2: launch classes bin ring sizes by powers of four, the
- * default; S = 1: by powers of two), "latency_split X" (an alignment
+ * "ring_bins S" (S = 2, the default: launch classes bin ring sizes by powers
+ * of four; S = 1: by powers of two, or by powers of four for a batch that
+ * would otherwise need more than 64 launches), "latency_split X" (an alignment
  * longer than X times the batch's estimated length moves to a 32-lane
  * variant; 0 = automatic) and "block_split X" (see RA_KERNEL_AUTO; 0, the
  * default, = never); create returns RA_EINVAL for other values.  None of

@@ -396,7 +396,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     // launch order and classes (variant x ring size), longest first
     std::vector<int> &order = h->plan_order;
     b.classes.clear();
-    if (!make_classes(items, n_items, order, b.classes, h->plan_sort))
+    if (!make_classes_binned(items, n_items, order, b.classes, h->plan_sort, h->plan.ring_bin_shift))
         return RA_EINVAL;
     if (b.plain)
         b.classes.clear();

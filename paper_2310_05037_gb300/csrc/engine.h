@@ -609,13 +609,14 @@ struct ServeState;
 // 32-lane variant (X <= 0: 0.5 for batches with few alignments per resident
 // group, else 1.0).
 struct PlanParams {
-    int ring_bin_shift = 2;
+    int ring_bin_shift = 2;     // 2: ring sizes in powers of four; 1: powers of two (falling back to
+                                // four for a batch that would need more than kMaxClasses launches)
     double latency_split = 0;
     bool split = true;          // the block-split kernel may be used (not with early termination)
     double split_factor = 0.0;  // "block_split X": an alignment whose time on one warp exceeds X times
                                 // the batch's balanced length (its work over all resident lanes)
                                 // goes to a block of four warps; 0 = never (the default: on the
-                                // long-read workload it measured slower, see the design notes)
+                                // long-read workload it measured slower than 32-lane groups)
 };
 
 }  // namespace ra_host
@@ -993,6 +994,24 @@ inline bool make_classes(const std::vector<PlanItem> &items, std::vector<int> &o
     const bool ok = make_classes(items.data(), items.size(), order, classes, scr, longest_first);
     order.resize(items.size());
     return ok;
+}
+
+// make_classes, and when the ring sizes binned by powers of two would need
+// more than kMaxClasses launches, the same with ring sizes binned by powers of
+// four (the items' ring sizes are recomputed; the block-split ones keep theirs).
+inline bool make_classes_binned(PlanItem *items, size_t n, std::vector<int> &order, std::vector<ClassLaunch> &classes,
+                                SortScratch &scr, int bin_shift, bool longest_first = true)
+{
+    if (make_classes(items, n, order, classes, scr, longest_first))
+        return true;
+    if (bin_shift >= 2)
+        return false;
+    parallel_for(n, [&](uint64_t lo, uint64_t hi) {
+        for (uint64_t x = lo; x < hi; ++x)
+            if (!items[x].split)
+                items[x].cap = ring_need(items[x].wd, kVariants[items[x].variant][0], 2);
+    });
+    return make_classes(items, n, order, classes, scr, longest_first);
 }
 
 // Ring entries one piece needs: the stripe period plus two (written one step

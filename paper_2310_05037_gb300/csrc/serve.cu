@@ -753,7 +753,8 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     std::vector<int> &order = sc_.order;
     std::vector<ClassLaunch> &classes = sc_.classes;
     classes.clear();
-    if (!make_classes(items.data(), items.size(), order, classes, sc_.sort, /*longest_first=*/false)) {
+    if (!make_classes_binned(items.data(), items.size(), order, classes, sc_.sort, h->plan.ring_bin_shift,
+                             /*longest_first=*/false)) {
         delete f;
         return RA_EINVAL;
     }

@@ -21,6 +21,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <numeric>
 #include <random>
@@ -336,6 +337,31 @@ int main()
                 ++cases;
             }
         }
+    }
+    // more launch classes than allowed with ring sizes binned by powers of
+    // two: the planner falls back to powers of four
+    {
+        std::vector<PlanItem> items;
+        for (int v = 0; v < kNumVariants; ++v)
+            for (int c = 0; c < 9; ++c) {
+                PlanItem it;
+                memset(&it.wd, 0, sizeof(WorkDesc));
+                it.variant = v;
+                it.wd.dC = (128 << c) - 2 - (c ? 1 : 0);  // ring_need: the next power of two at or above dC + 2
+                it.wd.s_end = 100;
+                it.cap = ring_need(it.wd, kVariants[v][0], 1);
+                it.cost = 100.0 * kVariants[v][0];
+                items.push_back(it);
+            }
+        std::vector<int> order;
+        std::vector<ClassLaunch> cls;
+        SortScratch scr;
+        CHECK(!make_classes(items.data(), items.size(), order, cls, scr), "expected more than kMaxClasses classes\n");
+        CHECK(make_classes_binned(items.data(), items.size(), order, cls, scr, 1), "fallback to coarser bins failed\n");
+        CHECK(cls.size() <= (size_t)kMaxClasses, "fallback still has too many classes\n");
+        for (const PlanItem &it : items)
+            CHECK(it.cap == ring_need(it.wd, kVariants[it.variant][0], 2), "fallback ring size\n");
+        ++cases;
     }
     // the arena allocator: live blocks never overlap and stay inside the
     // arena; once everything is released the whole arena is one free range
