@@ -361,99 +361,6 @@ inline Sched schedule(const BandDef &b, int64_t row0, int64_t nrows, int G, int 
     return s;
 }
 
-// The schedule of consecutive chunks of one candidate (serving): pieces of
-// `rows` rows starting at row0, row0 + rows, ... with one variant.  Instead
-// of the divisions of schedule() and the band edges per chunk, it keeps the
-// band's edge numerators at the next chunk's first row as quotient and
-// remainder by den, and steps them by precomputed increments.  The results
-// are the same as schedule(band, row0, rows, G, HR), band.lo and band.hi
-// (checked against them on the CPU).
-struct ChunkSched {
-    int64_t row0 = -1;               // first row of the next chunk (-1: not set up)
-    int64_t rows = 0;
-    int G = 0, HR = 0;
-    int64_t qx = 0, rx = 0;          // row0 * num - w * den = qx * den + rx, 0 <= rx < den
-    int64_t qy = 0, ry = 0;          // row0 * num + w * den = qy * den + ry
-    int64_t q1 = 0, r1 = 0;          // (rows - 1) * num = q1 * den + r1
-    int64_t qa = 0, ra = 0;          // rows * num
-    int64_t dC = 0, tail = 0;        // stripe period; kLag * t_last + (K - 1) * dC
-    int64_t rm = 0, qp = 0, rp = 0;  // with band.per: (row0 - 1) mod per, rows = qp * per + rp
-
-    void init(const BandDef &b, int64_t first_row, int64_t n, int g, int hr)
-    {
-        row0 = first_row;
-        rows = n;
-        G = g;
-        HR = hr;
-        const int64_t X = first_row * b.num - b.w * b.den, Y = first_row * b.num + b.w * b.den;
-        qx = fdiv(X, b.den);
-        rx = X - qx * b.den;
-        qy = fdiv(Y, b.den);
-        ry = Y - qy * b.den;
-        q1 = (n - 1) * b.num / b.den;
-        r1 = (n - 1) * b.num - q1 * b.den;
-        qa = n * b.num / b.den;
-        ra = n * b.num - qa * b.den;
-        const int64_t H = (int64_t)g * hr, K = (n + H - 1) / H;
-        int64_t span = fdiv(2 * b.w * b.den - (H - hr + 1) * b.num, b.den);
-        span = std::min<int64_t>(span, b.m - 1);
-        dC = std::max<int64_t>((int64_t)kLag * g + 3, span + 2);
-        tail = (int64_t)kLag * ((n - 1 - (K - 1) * H) / hr) + (K - 1) * dC;
-        if (b.per > 0) {
-            rm = (first_row - 1) - fdiv(first_row - 1, b.per) * b.per;
-            qp = n / b.per;
-            rp = n - qp * b.per;
-        }
-    }
-    // the chunk starting at row0: its schedule and the band of its last row
-    // (lo_last, hi_last, clipped to the table), then steps to the next chunk
-    void next(const BandDef &b, Sched &s, int64_t &lo_last, int64_t &hi_last, uint64_t &cells)
-    {
-        // in-band cells: away from the table's edges 2w per row plus the rows
-        // where row num / den is whole (the multiples of per, counted from
-        // the running remainder), else the floor sums
-        if (b.per > 0 && row0 + rows <= b.hi_row && row0 * b.num >= b.w * b.den - b.den + 1)
-            cells = (uint64_t)rows * (uint64_t)(2 * b.w) + (uint64_t)(qp + (rm + rp >= b.per ? 1 : 0));
-        else
-            cells = band_cells(b, row0, row0 + rows);
-        if (b.per > 0) {
-            rm += rp;
-            if (rm >= b.per)
-                rm -= b.per;
-        }
-        s = Sched();
-        const int64_t a0 = std::max<int64_t>(0, qx + (rx > 0 ? 1 : 0));
-        int64_t lx = qx + q1, lrx = rx + r1;
-        if (lrx >= b.den) {
-            lx += 1;
-            lrx -= b.den;
-        }
-        int64_t ly = qy + q1, lry = ry + r1;
-        if (lry >= b.den)
-            ly += 1;
-        lo_last = std::max<int64_t>(0, lx + (lrx > 0 ? 1 : 0));
-        hi_last = std::min<int64_t>(b.m - 1, ly);
-        s.a0 = (int32_t)a0;
-        if (a0 <= b.m - 1) {
-            s.dC = (int32_t)dC;
-            s.s_end = (int32_t)std::max<int64_t>(hi_last - a0 + 3 + tail, 1);
-        }
-        row0 += rows;
-        qx += qa;
-        rx += ra;
-        if (rx >= b.den) {
-            qx += 1;
-            rx -= b.den;
-        }
-        qy += qa;
-        ry += ra;
-        if (ry >= b.den) {
-            qy += 1;
-            ry -= b.den;
-        }
-    }
-};
-
 // ---------------------------------------------------------------- arena
 // Best-fit allocator over the caller's arena: free ranges indexed by offset
 // (to merge a released range with its neighbours) and by size (to find the

@@ -21,28 +21,25 @@
 #include <unordered_set>
 
 #include "engine.h"
+#include "serve_expand.cuh"
 
 namespace ra_host {
 
 struct ServeCand {
     BandDef band;
     int32_t w_report = 0;
-    uint64_t r_off = 0;     // floats from the arena base: expected signal (m values)
-    uint64_t fr_off[2] = {0, 0};  // floats from the arena base: frontier rows
-    uint32_t fr_cap = 0;    // floats per frontier row
-    int cur = 0;            // frontier holding the last processed row
-    int32_t fr_lo = -1, fr_wid = 0;  // its band (first column, width - 1)
     uint32_t m = 0;
-    bool dead = false;      // the band has left the table: no cell any more
+    uint64_t r_off = 0;           // floats from the arena base: expected signal (m values)
+    uint64_t fr_off[2] = {0, 0};  // floats from the arena base: frontier rows
+    uint32_t fr_cap = 0;          // floats per frontier row
     SigDesc sig{};
-    int64_t plan_rows = -1; // chunk height of the cached variant choice
-    int plan_variant = 0;   // variant chosen for chunks of plan_rows rows
-    ChunkSched csched;      // schedule of the next chunk of plan_rows rows, stepped without divisions
+    int cls = -1;                 // launch bucket (variant, ring size), set when the first chunk is planned
 };
 
 struct ServeRead {
     uint64_t read_id = 0;
-    void *block = nullptr;  // arena block: expected signals + frontiers
+    void *block = nullptr;  // arena block: candidate records, expected signals, frontiers
+    uint64_t rec_off = 0;   // bytes from the arena base to the candidate records (the block's start)
     uint32_t rows_done = 0;
     std::vector<ServeCand> cands;
     bool signal_done = false;
@@ -148,28 +145,21 @@ struct ServeState {
     }
     // a flush's planning arrays, kept across flushes (no allocation, no
     // first-touch page faults once they have grown)
-    struct Update {  // host state advanced only once the flush is launched
-        ServeCand *sc;
-        int32_t fr_lo, fr_wid;
-        bool dead;
-    };
     struct FlushScratch {
         std::vector<ServeRead *> rds;
-        std::vector<uint64_t> ev_first, item_first, sig_first;
+        std::vector<uint64_t> ev_first, item_first;
         std::vector<SigDesc> sig;
-        std::vector<PlanItem> items;
-        std::vector<int> read_of;
-        std::vector<Update> updates;
-        std::vector<int> order;
+        std::vector<uint64_t> init_off;
+        std::vector<ServeCandDev> init_rec;
+        std::vector<ServeChunkDev> chunks;
+        std::vector<int> cls_count, cls_map, cls_base;
         std::vector<ClassLaunch> classes;
-        SortScratch sort;
     } scratch;
     std::unordered_map<uint64_t, size_t> pending_at;           // read id -> index in pending
     uint64_t next_flush = 1;
     PinnedPool pinned;
     std::vector<cudaEvent_t> timing_events;  // reusable timing events
     std::map<ShapeKey, int> shape_variant;   // variant chosen per piece shape
-    std::mutex shape_mu;                     // guards shape_variant while a flush plans in parallel
     rawalign_dtw_serve_stats_t stats{};
 };
 
@@ -437,6 +427,11 @@ int submit_one(rawalign_dtw *h, ServeState *st, uint64_t read_id, const float *e
         }
         if (st->active >= st->slots)
             return RA_EAGAIN;
+        // the block starts with the candidates' device records (the state
+        // each chunk advances), then per candidate its expected signal and
+        // its two frontier rows
+        const uint64_t rec_floats = ((uint64_t)n_cands * sizeof(ServeCandDev) + 255) / 256 * 64;
+        floats += rec_floats;
         rd.block = h->arena.alloc(floats * sizeof(float));
         if (!rd.block) {
             reap_done(h, st);
@@ -444,7 +439,8 @@ int submit_one(rawalign_dtw *h, ServeState *st, uint64_t read_id, const float *e
             if (!rd.block)
                 return RA_EAGAIN;  // admission refused by free HBM in the arena
         }
-        uint64_t off = (uint64_t)((char *)rd.block - h->arena.base) / sizeof(float);
+        rd.rec_off = (uint64_t)((char *)rd.block - h->arena.base);
+        uint64_t off = rd.rec_off / sizeof(float) + rec_floats;
         for (auto &sc : rd.cands) {
             sc.r_off = off;
             sc.sig.r_off = off;
@@ -568,175 +564,111 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     if (st->n_pending == 0)
         return RA_OK;
     const auto t_plan = std::chrono::steady_clock::now();
-    // plan: one piece of work per (chunk, candidate).  A first pass places
-    // every chunk's events, pieces and signal descriptors (prefix sums) and
-    // registers its tickets; the second fills the records (on the host
-    // worker threads when the flush is large).  Each read has at most one
-    // pending chunk, so the chunks touch disjoint read state; only the
-    // handle-wide shape cache is shared (under a lock).
+    // plan: the host places every chunk's events and pieces (prefix sums),
+    // registers its tickets, gives each new candidate its variant and launch
+    // bucket and counts the pieces per bucket; the device then builds each
+    // piece's work record from the chunk record and the candidate's carried
+    // state (serve_piece), so nothing here is done per piece
     FlushRec *f = new FlushRec();
-    using Update = ServeState::Update;
     ServeState::FlushScratch &sc_ = st->scratch;
     const size_t n_pend = st->n_pending;
+    const int n_keys_cls = kNumVariants * kServeCaps;
     std::vector<ServeRead *> &rds = sc_.rds;
-    std::vector<uint64_t> &ev_first = sc_.ev_first, &item_first = sc_.item_first, &sig_first = sc_.sig_first;
+    std::vector<uint64_t> &ev_first = sc_.ev_first, &item_first = sc_.item_first;
+    std::vector<SigDesc> &sig = sc_.sig;
+    std::vector<uint64_t> &init_off = sc_.init_off;
+    std::vector<ServeCandDev> &init_rec = sc_.init_rec;
+    std::vector<ServeChunkDev> &chunks = sc_.chunks;
+    std::vector<int> &cls_count = sc_.cls_count, &cls_map = sc_.cls_map, &cls_base = sc_.cls_base;
     rds.resize(n_pend);
     ev_first.assign(n_pend + 1, 0);
     item_first.assign(n_pend + 1, 0);
-    sig_first.assign(n_pend + 1, 0);
+    sig.clear();
+    init_off.clear();
+    init_rec.clear();
+    chunks.resize(n_pend);
+    cls_count.assign(n_keys_cls, 0);
+    // ring sizes of serving buckets: powers of four at least, so that the
+    // buckets of ten variants stay few
+    const int bin_shift = std::max(2, h->plan.ring_bin_shift);
     for (size_t ci = 0; ci < n_pend; ++ci) {
         const PendingChunk &pc = st->pending[ci];
         ServeRead &rd = st->reads.at(pc.read_id);
         rds[ci] = &rd;
         const uint64_t nrows = pc.ev.size();
-        const uint64_t count = nrows ? rd.cands.size() : 0;  // a close-only chunk returns nothing
+        const uint32_t count = nrows ? (uint32_t)rd.cands.size() : 0;  // a close-only chunk returns nothing
         ev_first[ci + 1] = ev_first[ci] + nrows;
         item_first[ci + 1] = item_first[ci] + count;
-        sig_first[ci + 1] = sig_first[ci] + (rd.signal_done ? 0 : count);
         for (uint64_t t : pc.tickets)
-            f->tickets.push_back({t, pc.read_id, (uint32_t)item_first[ci], (uint32_t)count, pc.last});
+            f->tickets.push_back({t, pc.read_id, (uint32_t)item_first[ci], count, pc.last});
         if (pc.last)
             f->closing.push_back(pc.read_id);
+        ServeChunkDev &ch = chunks[ci];
+        ch.ev_off = ev_first[ci];
+        ch.cand_off = rd.rec_off;
+        ch.n_cands = count;
+        ch.first_piece = (uint32_t)item_first[ci];
+        ch.row0 = (int32_t)rd.rows_done;
+        ch.nrows = (int32_t)nrows;
+        for (uint32_t c = 0; c < count; ++c) {
+            ServeCand &sc = rd.cands[c];
+            if (sc.cls < 0) {
+                // first chunk of the candidate: its variant (cached per shape
+                // across reads) and its launch bucket, then its device record
+                const ShapeKey key{(int64_t)nrows, sc.band.num, sc.band.den, sc.band.w, sc.band.m};
+                int v;
+                auto hit = st->shape_variant.find(key);
+                if (hit != st->shape_variant.end()) {
+                    v = hit->second;
+                } else {
+                    Sched sch;
+                    v = choose_variant(sc.band, rd.rows_done, (int64_t)nrows, sch, h->slot_cost);
+                    if (st->shape_variant.size() < 4096)
+                        st->shape_variant[key] = v;
+                }
+                const int G = kVariants[v][0], HR = kVariants[v][1];
+                const int64_t H = (int64_t)G * HR;
+                int64_t span = fdiv(2 * sc.band.w * sc.band.den - (H - HR + 1) * sc.band.num, sc.band.den);
+                span = std::min<int64_t>(span, sc.band.m - 1);
+                const int64_t dC = std::max<int64_t>((int64_t)kLag * G + 3, span + 2);
+                // ring: the stripe period and the widest stored row above
+                const int64_t need =
+                    std::max<int64_t>(dC + 2, std::min<int64_t>(2 * sc.band.w, sc.band.m - 1) + (int64_t)kLag * G + 4);
+                // (admission keeps m below 2^30, so 2^30 entries always suffice)
+                int cap_i = 0;
+                while ((128ll << cap_i) < need && cap_i < kServeCaps - 1)
+                    cap_i = std::min(cap_i + bin_shift, kServeCaps - 1);
+                sc.cls = v * kServeCaps + cap_i;
+                ServeCandDev d{};
+                d.r_off = sc.r_off;
+                d.fr_off[0] = sc.fr_off[0];
+                d.fr_off[1] = sc.fr_off[1];
+                d.num = sc.band.num;
+                d.den = sc.band.den;
+                d.per = sc.band.per;
+                d.hi_row = sc.band.hi_row;
+                d.m = (int32_t)sc.m;
+                d.w = (int32_t)sc.band.w;
+                d.w_report = sc.w_report;
+                d.G = G;
+                d.HR = HR;
+                d.dC = (int32_t)dC;
+                d.cls = sc.cls;
+                d.cur = 0;
+                d.fr_lo = -1;
+                d.fr_wid = 0;
+                d.dead = 0;
+                init_off.push_back(rd.rec_off + (uint64_t)c * sizeof(ServeCandDev));
+                init_rec.push_back(d);
+            }
+            if (!rd.signal_done)
+                sig.push_back(sc.sig);
+            cls_count[sc.cls]++;
+        }
     }
     const uint32_t chunk_idx = (uint32_t)n_pend;
     const uint64_t n_ev = ev_first[n_pend];
-    std::vector<SigDesc> &sig = sc_.sig;
-    std::vector<PlanItem> &items = sc_.items;
-    std::vector<int> &read_of = sc_.read_of;
-    std::vector<Update> &updates = sc_.updates;
-    sig.resize(sig_first[n_pend]);
-    items.resize(item_first[n_pend]);
-    read_of.resize(item_first[n_pend]);
-    updates.resize(item_first[n_pend]);
-    auto plan_chunk = [&](size_t ci) {
-        const PendingChunk &pc = st->pending[ci];
-        ServeRead &rd = *rds[ci];
-        const uint32_t row0 = rd.rows_done, nrows = (uint32_t)pc.ev.size();
-        const uint64_t ev_off = ev_first[ci];
-        const uint32_t first = (uint32_t)item_first[ci];
-        const uint32_t count = (uint32_t)(item_first[ci + 1] - first);
-        for (uint32_t c = 0; c < count; ++c) {
-            ServeCand &sc = rd.cands[c];
-            if (!rd.signal_done)
-                sig[sig_first[ci] + c] = sc.sig;
-            PlanItem &it = items[first + c];
-            memset(&it.wd, 0, sizeof(WorkDesc));
-            it.wave = 0;
-            it.split = false;
-            WorkDesc &wd = it.wd;
-            wd.ev_off = ev_off;
-            wd.r_off = sc.r_off;
-            wd.num = sc.band.num;
-            wd.den = sc.band.den;
-            wd.row0 = (int32_t)row0;
-            wd.nrows = (int32_t)nrows;
-            wd.m = (int32_t)sc.m;
-            wd.w = (int32_t)sc.band.w;
-            wd.cand = (int32_t)(first + c);
-            wd.read = (int32_t)ci;
-            wd.n_read = (int32_t)(row0 + nrows);
-            wd.w_report = sc.w_report;
-            if (row0 == 0) {
-                wd.fin_off = ~0ull;
-                wd.fin_lo = -1;
-                wd.fin_wid = 0;
-            } else {
-                wd.fin_off = sc.fr_off[sc.cur];
-                wd.fin_lo = sc.fr_lo;
-                wd.fin_wid = sc.fr_wid;
-            }
-            wd.fout_off = sc.fr_off[1 - sc.cur];
-            const int64_t last_row = (int64_t)row0 + nrows - 1;
-            int64_t lo_last = -1, hi_last = -1;  // band of the last row (computed below)
-            uint64_t cells = UINT64_MAX;          // in-band cells (computed below)
-            Sched sch;
-            if (sc.dead) {
-                it.variant = 0;
-                sch.s_end = 0;
-            } else if (sc.plan_rows == (int64_t)nrows) {
-                // chunks of one height get one variant: the choice hardly
-                // depends on where the rows start (the results never do);
-                // their schedules follow from the previous chunk's
-                it.variant = sc.plan_variant;
-                const int G = kVariants[it.variant][0], HR = kVariants[it.variant][1];
-                if (sc.csched.row0 != (int64_t)row0 || sc.csched.rows != (int64_t)nrows || sc.csched.G != G ||
-                    sc.csched.HR != HR)
-                    sc.csched.init(sc.band, row0, nrows, G, HR);
-                sc.csched.next(sc.band, sch, lo_last, hi_last, cells);
-                if (sch.s_end <= 0)
-                    it.variant = 0;
-            } else {
-                // candidates of one shape (chunk height, band, table width)
-                // share one choice across reads: a small handle-wide cache
-                const ShapeKey key{(int64_t)nrows, sc.band.num, sc.band.den, sc.band.w, sc.band.m};
-                int cached = -1;
-                {
-                    std::lock_guard<std::mutex> lk(st->shape_mu);
-                    auto hit = st->shape_variant.find(key);
-                    if (hit != st->shape_variant.end())
-                        cached = hit->second;
-                }
-                if (cached >= 0) {
-                    it.variant = cached;
-                    sch = schedule(sc.band, row0, nrows, kVariants[it.variant][0], kVariants[it.variant][1]);
-                } else {
-                    it.variant = choose_variant(sc.band, row0, nrows, sch, h->slot_cost);
-                    if (sch.s_end > 0) {
-                        std::lock_guard<std::mutex> lk(st->shape_mu);
-                        if (st->shape_variant.size() < 4096)
-                            st->shape_variant[key] = it.variant;
-                    }
-                }
-                if (sch.s_end <= 0) {
-                    it.variant = 0;
-                } else {
-                    sc.plan_rows = nrows;
-                    sc.plan_variant = it.variant;
-                    sc.csched.init(sc.band, (int64_t)row0 + nrows, nrows, kVariants[it.variant][0],
-                                   kVariants[it.variant][1]);
-                }
-            }
-            if (lo_last < 0) {
-                lo_last = sc.band.lo(last_row);
-                hi_last = sc.band.hi(last_row);
-            }
-            wd.fout_lo = (int32_t)lo_last;
-            wd.dC = sch.dC;
-            wd.a0 = sch.a0;
-            wd.s_end = sch.s_end;
-            if (sch.s_end <= 0)
-                cells = 0;
-            else if (cells == UINT64_MAX)
-                cells = band_cells(sc.band, row0, (int64_t)row0 + nrows);
-            wd.cells = cells;
-            it.cost = (double)sch.s_end * kVariants[it.variant][0];
-            it.cap = ring_need(wd, kVariants[it.variant][0], h->plan.ring_bin_shift);
-            read_of[first + c] = (int)ci;
-            // the band of this piece's last row is the row above the next piece
-            Update u{&sc, sc.fr_lo, sc.fr_wid, sc.dead};
-            if (!sc.dead) {
-                if (hi_last >= lo_last && sch.s_end > 0) {
-                    u.fr_lo = (int32_t)lo_last;
-                    u.fr_wid = (int32_t)(hi_last - lo_last);
-                } else {
-                    u.dead = true;
-                }
-            }
-            updates[first + c] = u;
-        }
-    };
-    {
-        // one thread unless the flush is large: waking the worker threads
-        // costs more than planning a few thousand pieces (measured on GB300's
-        // host: 121 GCUPS served with one thread, 103 with sixteen)
-        const unsigned T = (unsigned)std::min<size_t>(
-            {(size_t)host_threads(), n_pend, std::max<size_t>(1, (size_t)item_first[n_pend] / 32768)});
-        run_tasks(T, [&](unsigned t) {
-            for (size_t ci = n_pend * t / T; ci < n_pend * (t + 1) / T; ++ci)
-                plan_chunk(ci);
-        });
-    }
-    const uint32_t n_items = (uint32_t)items.size();
+    const uint32_t n_items = (uint32_t)item_first[n_pend];
     if (n_items == 0) {
         // only close-only chunks: nothing to run
         f->h_res = nullptr;
@@ -750,14 +682,52 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         st->pending_at.clear();
         return RA_OK;
     }
-    std::vector<int> &order = sc_.order;
+    // launch classes: one per bucket in use, its pieces contiguous in the
+    // work array; with more buckets than launches, one class per variant with
+    // the variant's largest ring
     std::vector<ClassLaunch> &classes = sc_.classes;
     classes.clear();
-    if (!make_classes_binned(items.data(), items.size(), order, classes, sc_.sort, h->plan.ring_bin_shift,
-                             /*longest_first=*/false)) {
-        delete f;
-        return RA_EINVAL;
+    cls_map.assign(n_keys_cls, 0);
+    cls_base.clear();
+    int n_used = 0;
+    for (int key = 0; key < n_keys_cls; ++key)
+        n_used += cls_count[key] > 0;
+    const bool per_variant = n_used > kMaxClasses;
+    {
+        for (int v = 0; v < kNumVariants; ++v) {
+            int merged = -1;
+            for (int ci = 0; ci < kServeCaps; ++ci) {
+                const int key = v * kServeCaps + ci;
+                if (!cls_count[key])
+                    continue;
+                if (per_variant && merged >= 0) {
+                    ClassLaunch &cl = classes[merged];
+                    cl.count += cls_count[key];
+                    cl.ring_cap = 128 << ci;  // keys ascend: the largest ring so far
+                    cl.max_cost = cl.count;
+                    cls_map[key] = merged;
+                    continue;
+                }
+                ClassLaunch cl;
+                cl.G = kVariants[v][0];
+                cl.HR = kVariants[v][1];
+                cl.ring_cap = 128 << ci;
+                cl.count = cls_count[key];
+                cl.max_cost = cl.count;
+                cls_map[key] = (int)classes.size();
+                if (per_variant)
+                    merged = (int)classes.size();
+                classes.push_back(cl);
+            }
+        }
+        int base = 0;
+        for (auto &cl : classes) {
+            cl.first = base;
+            cls_base.push_back(base);
+            base += cl.count;
+        }
     }
+    const int n_classes = (int)classes.size();
     // device memory for this flush
     auto take = [&](uint64_t bytes) -> void * {
         void *p = h->arena.alloc(std::max<uint64_t>(bytes, 256));
@@ -766,15 +736,24 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         return p;
     };
     // the flush's inputs live in one arena block and travel in one copy:
-    // events, signal descriptors, work records, read slots, and the zeroed
-    // per-chunk best keys and queue counters
+    // events, signal descriptors, new candidates, chunk records, the bucket
+    // map and bases, and the zeroed bucket counters, per-chunk best keys and
+    // queue counters; the work records and read slots that the device builds
+    // follow in the same block
     auto al256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t n_init = init_off.size();
     const size_t b_ev = sizeof(float) * n_ev, b_sig = sizeof(SigDesc) * sig.size();
-    const size_t b_work = sizeof(WorkDesc) * n_items, b_rd = sizeof(int) * n_items;
+    const size_t b_iidx = sizeof(uint64_t) * n_init, b_irec = sizeof(ServeCandDev) * n_init;
+    const size_t b_ch = sizeof(ServeChunkDev) * n_pend, b_map = sizeof(int) * n_keys_cls;
+    const size_t b_base = sizeof(int) * (size_t)std::max(n_classes, 1), b_fill = b_base;
     const size_t b_keys = sizeof(unsigned long long) * chunk_idx, b_q = sizeof(int) * (kMaxClasses + 2);
-    const size_t o_sig = al256(b_ev), o_work = o_sig + al256(b_sig), o_rd = o_work + al256(b_work);
-    const size_t o_keys = o_rd + al256(b_rd), o_q = o_keys + al256(b_keys), in_bytes = o_q + al256(b_q);
-    char *d_in = (char *)take(in_bytes);
+    const size_t b_work = sizeof(WorkDesc) * n_items, b_rd = sizeof(int) * n_items;
+    const size_t o_sig = al256(b_ev), o_iidx = o_sig + al256(b_sig), o_irec = o_iidx + al256(b_iidx);
+    const size_t o_ch = o_irec + al256(b_irec), o_map = o_ch + al256(b_ch), o_base = o_map + al256(b_map);
+    const size_t o_fill = o_base + al256(b_base), o_keys = o_fill + al256(b_fill), o_q = o_keys + al256(b_keys);
+    const size_t in_bytes = o_q + al256(b_q);  // copied from the host
+    const size_t o_work = in_bytes, o_rd = o_work + al256(b_work), all_bytes = o_rd + al256(b_rd);
+    char *d_in = (char *)take(all_bytes);
     f->d_res = (rawalign_result_t *)take(sizeof(rawalign_result_t) * n_items);
     bool ok = d_in && f->d_res;
     if (ok)
@@ -790,37 +769,36 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
             h->arena.release(p);
         st->pinned.put(f->h_in);
         st->pinned.put(f->h_res);
+        // the new candidates are planned again with the next flush
+        for (size_t ci = 0; ci < n_pend; ++ci)
+            if (!rds[ci]->signal_done)
+                for (auto &sc : rds[ci]->cands)
+                    sc.cls = -1;
         delete f;
         return RA_ENOMEM;
     }
+    char *hin = (char *)f->h_in;
+    for (size_t ci = 0; ci < n_pend; ++ci) {
+        const PendingChunk &pc = st->pending[ci];
+        if (!pc.ev.empty())
+            memcpy(hin + sizeof(float) * ev_first[ci], pc.ev.data(), sizeof(float) * pc.ev.size());
+    }
+    if (b_sig)
+        memcpy(hin + o_sig, sig.data(), b_sig);
+    if (n_init) {
+        memcpy(hin + o_iidx, init_off.data(), b_iidx);
+        memcpy(hin + o_irec, init_rec.data(), b_irec);
+    }
+    memcpy(hin + o_ch, chunks.data(), b_ch);
+    memcpy(hin + o_map, cls_map.data(), b_map);
+    memcpy(hin + o_base, cls_base.data(), sizeof(int) * n_classes);
+    memset(hin + o_fill, 0, in_bytes - o_fill);
     float *d_ev = (float *)d_in;
     SigDesc *d_sig = (SigDesc *)(d_in + o_sig);
     WorkDesc *d_work = (WorkDesc *)(d_in + o_work);
     int *d_read_of = (int *)(d_in + o_rd);
     unsigned long long *d_keys = (unsigned long long *)(d_in + o_keys);
     int *d_queue = (int *)(d_in + o_q);
-    char *hin = (char *)f->h_in;
-    {
-        // pack the pinned input block on the worker threads: each takes a
-        // range of chunks (their events) and a range of work records (in
-        // launch order)
-        WorkDesc *hw = (WorkDesc *)(hin + o_work);
-        float *hev = (float *)hin;
-        const unsigned T = (unsigned)std::min<size_t>(
-            {(size_t)host_threads(), n_pend, std::max<size_t>(1, (size_t)n_items / 32768)});
-        run_tasks(T, [&](unsigned t) {
-            for (size_t ci = n_pend * t / T; ci < n_pend * (t + 1) / T; ++ci) {
-                const PendingChunk &pc = st->pending[ci];
-                if (!pc.ev.empty())
-                    memcpy(hev + ev_first[ci], pc.ev.data(), sizeof(float) * pc.ev.size());
-            }
-            for (size_t x = (size_t)n_items * t / T; x < (size_t)n_items * (t + 1) / T; ++x)
-                hw[x] = items[order[x]].wd;
-        });
-    }
-    memcpy(hin + o_sig, sig.data(), b_sig);
-    memcpy(hin + o_rd, read_of.data(), b_rd);
-    memset(hin + o_keys, 0, in_bytes - o_keys);
     cudaStream_t s = h->stream;
     const auto t_launch = std::chrono::steady_clock::now();
     st->stats.host_plan_ms += std::chrono::duration<double, std::milli>(t_launch - t_plan).count();
@@ -840,10 +818,15 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     RA_CUDA(cudaMemcpyAsync(d_in, hin, in_bytes, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaEventRecord(f->t_ev[1], s));
     float *abase = (float *)h->arena.base;
+    RA_CUDA(launch_serve_init(h->arena.base, (const uint64_t *)(d_in + o_iidx), (const ServeCandDev *)(d_in + o_irec),
+                              (int)n_init, s));
     if (!sig.empty())
         RA_CUDA(launch_expected_signal(d_sig, (int)sig.size(), h->d_ref, h->d_pore, h->cfg.k, abase, s));
+    RA_CUDA(launch_serve_expand((const ServeChunkDev *)(d_in + o_ch), (int)n_pend, h->arena.base,
+                                (const int *)(d_in + o_map), (const int *)(d_in + o_base), (int *)(d_in + o_fill),
+                                d_work, d_read_of, s));
     RA_CUDA(cudaEventRecord(h->fork, s));
-    for (size_t ci = 0; ci < classes.size(); ++ci) {
+    for (int ci = 0; ci < n_classes; ++ci) {
         auto &cl = classes[ci];
         cudaStream_t cs = h->aux[ci];
         RA_CUDA(cudaStreamWaitEvent(cs, h->fork, 0));
@@ -881,14 +864,8 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     RA_CUDA(cudaMemcpyAsync(f->h_res + n_items, d_queue + kMaxClasses, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
 #endif
     RA_CUDA(cudaEventRecord(f->done, s));
-    // launched: advance the host-side read state
-    for (auto &u : updates) {
-        if (!u.sc->dead)
-            u.sc->cur = 1 - u.sc->cur;
-        u.sc->fr_lo = u.fr_lo;
-        u.sc->fr_wid = u.fr_wid;
-        u.sc->dead = u.dead;
-    }
+    // launched: advance the host-side read state (the candidates' frontier
+    // state advances on the device)
     for (size_t ci = 0; ci < n_pend; ++ci) {
         ServeRead &rd = *rds[ci];
         rd.signal_done = true;

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "serve_expand.cuh"
 
 using namespace ra_host;
 
@@ -297,43 +298,86 @@ int main()
         }
         cases += cell_cases;
     }
-    // serving's incremental chunk schedule against schedule() and the band
-    // edges computed directly, over runs of consecutive chunks
+    // serving: the work records the device builds per piece (serve_piece)
+    // against the host planner's schedule, band edges and cell count, over
+    // runs of consecutive chunks with the frontier state carried along
     {
         for (int rep = 0; rep < 20000; ++rep) {
             BandDef b;
             b.m = 1 + (int64_t)(rng() % 6000);
-            b.num = 1 + (int64_t)(rng() % 3000);
+            b.num = (rep % 97 == 0) ? 0 : 1 + (int64_t)(rng() % 3000);
             b.den = 1 + (int64_t)(rng() % 3000);
             b.w = 1 + (int64_t)(rng() % 200);
-            if (rep % 500 == 0) {
-                b.num = 1 + (int64_t)(rng() % (1ll << 30));
-                b.den = 1 + (int64_t)(rng() % (1ll << 30));
-            }
-            const int v = (int)(rng() % kNumVariants);
-            const int G = kVariants[v][0], HR = kVariants[v][1];
-            const int64_t rows = 1 + (int64_t)(rng() % 400);
-            int64_t row0 = (int64_t)(rng() % 3000);
             if (rng() % 2)
                 prepare_cell_count(b);
-            ChunkSched cs;
-            cs.init(b, row0, rows, G, HR);
-            for (int c = 0; c < 30; ++c, row0 += rows) {
-                Sched got;
-                int64_t lo_last, hi_last;
-                uint64_t cells;
-                cs.next(b, got, lo_last, hi_last, cells);
-                CHECK(cells == band_cells(b, row0, row0 + rows), "chunk cells num %lld den %lld w %lld m %lld\n",
-                      (long long)b.num, (long long)b.den, (long long)b.w, (long long)b.m);
-                const Sched want = schedule(b, row0, rows, G, HR);
+            const int v = (int)(rng() % kNumVariants);
+            const int G = kVariants[v][0], HR = kVariants[v][1];
+            ServeCandDev s{};
+            s.r_off = 1000;
+            s.fr_off[0] = 5000;
+            s.fr_off[1] = 9000;
+            s.num = b.num;
+            s.den = b.den;
+            s.per = b.per;
+            s.hi_row = b.hi_row;
+            s.m = (int32_t)b.m;
+            s.w = (int32_t)b.w;
+            s.w_report = 7;
+            s.G = G;
+            s.HR = HR;
+            s.fr_lo = -1;
+            // the stripe period as the planner sets it
+            s.dC = schedule(b, 0, 1, G, HR).dC;
+            {
+                const int64_t H = (int64_t)G * HR;
+                int64_t span = fdiv(2 * b.w * b.den - (H - HR + 1) * b.num, b.den);
+                span = std::min<int64_t>(span, b.m - 1);
+                s.dC = (int32_t)std::max<int64_t>((int64_t)kLag * G + 3, span + 2);
+            }
+            int cur = 0, fr_lo = -1, fr_wid = 0;
+            bool dead = false;
+            int64_t row0 = 0;
+            for (int c = 0; c < 25; ++c) {
+                const int64_t rows = 1 + (int64_t)(rng() % 300);
+                ServeChunkDev ch{};
+                ch.ev_off = 123;
+                ch.cand_off = 0;
+                ch.n_cands = 1;
+                ch.first_piece = 40;
+                ch.row0 = (int32_t)row0;
+                ch.nrows = (int32_t)rows;
+                WorkDesc wd{};
+                serve_piece(ch, 3, 0, s, wd);
                 const int64_t last = row0 + rows - 1;
-                CHECK(got.a0 == want.a0 && got.s_end == want.s_end && got.dC == want.dC && lo_last == b.lo(last) &&
-                          hi_last == b.hi(last),
-                      "chunk schedule num %lld den %lld w %lld m %lld rows %lld row0 %lld G %d HR %d: "
-                      "a0 %d/%d s_end %d/%d dC %d/%d lo %lld/%lld hi %lld/%lld\n",
-                      (long long)b.num, (long long)b.den, (long long)b.w, (long long)b.m, (long long)rows,
-                      (long long)row0, G, HR, got.a0, want.a0, got.s_end, want.s_end, got.dC, want.dC,
-                      (long long)lo_last, (long long)b.lo(last), (long long)hi_last, (long long)b.hi(last));
+                Sched want;
+                if (!dead)
+                    want = schedule(b, row0, rows, G, HR);
+                const uint64_t cells = want.s_end > 0 ? band_cells(b, row0, row0 + rows) : 0;
+                const bool fin_ok = row0 == 0 ? (wd.fin_off == ~0ull && wd.fin_lo == -1 && wd.fin_wid == 0)
+                                              : (wd.fin_off == (uint64_t)(cur ? 9000 : 5000) && wd.fin_lo == fr_lo &&
+                                                 wd.fin_wid == fr_wid);
+                CHECK(fin_ok && wd.fout_off == (uint64_t)(cur ? 5000 : 9000) && wd.fout_lo == (int32_t)b.lo(last) &&
+                          wd.a0 == want.a0 && wd.s_end == want.s_end && wd.dC == want.dC && wd.cells == cells &&
+                          wd.cand == 40 && wd.read == 3 && wd.n_read == (int32_t)(row0 + rows) && wd.m == (int32_t)b.m,
+                      "serve_piece num %lld den %lld w %lld m %lld row0 %lld rows %lld: a0 %d/%d s_end %d/%d dC %d/%d "
+                      "cells %llu/%llu\n",
+                      (long long)b.num, (long long)b.den, (long long)b.w, (long long)b.m, (long long)row0,
+                      (long long)rows, wd.a0, want.a0, wd.s_end, want.s_end, wd.dC, want.dC,
+                      (unsigned long long)wd.cells, (unsigned long long)cells);
+                // the host planner's frontier update
+                if (!dead) {
+                    cur = 1 - cur;
+                    const int64_t lo = b.lo(last), hi = b.hi(last);
+                    if (hi >= lo && want.s_end > 0) {
+                        fr_lo = (int32_t)lo;
+                        fr_wid = (int32_t)(hi - lo);
+                    } else {
+                        dead = true;
+                    }
+                }
+                CHECK(s.cur == cur && s.fr_lo == fr_lo && s.fr_wid == fr_wid && (s.dead != 0) == dead,
+                      "serve_piece state\n");
+                row0 += rows;
                 ++cases;
             }
         }
