@@ -39,5 +39,15 @@ static __device__ __forceinline__ void floordivmod(long long x, long long d, lon
     }
 }
 
+// Programmatic dependent launch (sm_90 and later).  pdl_allow_next lets the
+// next kernel of the stream, when it is launched as a programmatic
+// dependent, start its blocks as soon as SM slots free up; every block calls
+// it first, so all blocks of this grid are resident by then.  pdl_wait_prev
+// waits until the previous kernel of the stream has completed; a grid whose
+// block 0 calls it before exiting completes after its predecessor, so the
+// completion of the last kernel of a chain implies that of all of them.
+// Both do nothing in a kernel that was not launched as a dependent.
+static __device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+static __device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 }  // namespace ra

@@ -533,7 +533,6 @@ using namespace ra_host;
 struct rawalign_dtw {
     rawalign_dtw_config_t cfg{};
     cudaStream_t stream = nullptr;
-    cudaStream_t aux[kMaxClasses] = {};   // one graph branch per launch class
     cudaStream_t upload = nullptr;         // batch uploads: overlap the previous batch's kernels
     cudaEvent_t uploaded = nullptr;
     char *stage = nullptr;                 // pinned host staging for planned records (grown on demand)
@@ -541,7 +540,6 @@ struct rawalign_dtw {
     std::vector<ra_host::PlanItem> plan_items;  // planning scratch, reused across batches
     std::vector<int> plan_order;
     ra_host::SortScratch plan_sort;
-    cudaEvent_t fork = nullptr, join[kMaxClasses] = {};
     int device = 0;
     int sm_count = 152;
     Arena arena;

@@ -101,14 +101,18 @@ struct CombineDesc {
 cudaError_t launch_expected_signal(const SigDesc *d, int n, const uint8_t *ref2bit, const float *pore,
                                    int k, float *r_all, cudaStream_t s);
 cudaError_t launch_check_events(const float *ev, uint64_t n, int *err, cudaStream_t s);
+// dependent: launched as a programmatic dependent of the stream's previous
+// kernel (its blocks start as SM slots free up; see pdl_allow_next)
 cudaError_t launch_stripe(int G, int HR, const StripeParams &p, int grid, int block, size_t smem,
-                          cudaStream_t s);
+                          cudaStream_t s, bool dependent = false);
+cudaError_t launch_maybe_dependent(const void *fn, int grid, int block, size_t smem, cudaStream_t s, void **args,
+                                   bool dependent);
 int stripe_max_blocks_per_sm(int G, int HR, int block, size_t smem);
 // the block-split kernel for long alignments (split_kernel.cu): four warps,
 // HR rows per lane, one alignment per block
 int split_max_blocks_per_sm(int HR);
 size_t split_smem_bytes();
-cudaError_t launch_split(int HR, const StripeParams &p, int grid, cudaStream_t s);
+cudaError_t launch_split(int HR, const StripeParams &p, int grid, cudaStream_t s, bool dependent = false);
 void *pick_stripe_et(int G, int HR, bool smem_ring);  // stripe_kernel_et.cu
 cudaError_t launch_plain(const WorkDesc *w, const float *events, const float *r_all, float *diag,
                          rawalign_result_t *results, unsigned long long *best_keys, float b_match,

@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(128, 4) dtw_split_kernel(const StripeParams p)
     const int wprev = (w + kSplitWarps - 1) % kSplitWarps;
     // this block's bottom-row buffers: [warp][2][ring_cap] floats
     float *gbuf = p.gring + (size_t)blockIdx.x * kSplitWarps * 2 * p.ring_cap;
+    pdl_allow_next();  // launch classes queue one after another in one stream
 
     while (true) {
         if (threadIdx.x == 0) {
@@ -86,8 +87,11 @@ __global__ void __launch_bounds__(128, 4) dtw_split_kernel(const StripeParams p)
             sh.tag[threadIdx.x >> 1][threadIdx.x & 1] = ~0ull;  // no stripe yet
         __syncthreads();
         const int item = sh.item;
-        if (item >= p.n_work)
+        if (item >= p.n_work) {
+            if (blockIdx.x == 0)
+                pdl_wait_prev();  // complete after the launch class queued before this one
             return;
+        }
         const WorkDesc wd = p.work[item];
         const int nrows = wd.nrows, m = wd.m;
         const long long num = wd.num, dn = wd.den, wb = wd.w;
@@ -383,7 +387,7 @@ int split_max_blocks_per_sm(int HR)
     return nb;
 }
 
-cudaError_t launch_split(int HR, const StripeParams &p, int grid, cudaStream_t s)
+cudaError_t launch_split(int HR, const StripeParams &p, int grid, cudaStream_t s, bool dependent)
 {
     void *fn = pick_split(HR, p.end_free != 0);
     if (!fn)
@@ -393,7 +397,7 @@ cudaError_t launch_split(int HR, const StripeParams &p, int grid, cudaStream_t s
     if (e != cudaSuccess)
         return e;
     void *args[] = {(void *)&p};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(128), args, smem, s);
+    return launch_maybe_dependent(fn, grid, 128, smem, s, args, dependent);
 }
 
 }  // namespace ra

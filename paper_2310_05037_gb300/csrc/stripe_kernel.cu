@@ -81,7 +81,7 @@ int stripe_max_blocks_uncached(int G, int HR, int block, size_t smem)
 }
 
 cudaError_t launch_stripe(int G, int HR, const StripeParams &p, int grid, int block, size_t smem,
-                          cudaStream_t s)
+                          cudaStream_t s, bool dependent)
 {
     void *fn = p.early_term ? pick_stripe_et(G, HR, p.ring_in_smem != 0)
                             : pick_stripe(G, HR, p.end_free != 0, p.ring_in_smem != 0);
@@ -93,7 +93,23 @@ cudaError_t launch_stripe(int G, int HR, const StripeParams &p, int grid, int bl
             return e;
     }
     void *args[] = {(void *)&p};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
+    return launch_maybe_dependent(fn, grid, block, smem, s, args, dependent);
+}
+
+cudaError_t launch_maybe_dependent(const void *fn, int grid, int block, size_t smem, cudaStream_t s, void **args,
+                                   bool dependent)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = dependent ? 1 : 0;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace ra

@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
     const int rmask = p.ring_cap - 1;
     GroupCold *gc = gcs + gw;
     LaneCold *lc = lcs + threadIdx.x;
+    pdl_allow_next();  // launch classes queue one after another in one stream
 
     // hot state
     const float *rr = p.r_all;
@@ -674,6 +675,8 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
             }
         }
     }
+    if (blockIdx.x == 0)
+        pdl_wait_prev();  // complete after the launch class queued before this one
 }
 
 }  // namespace ra
