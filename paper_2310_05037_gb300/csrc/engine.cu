@@ -482,15 +482,18 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
                 ++launches;
             }
         } else {
-            // launch classes queue one after another on the stream, longest
-            // first, each launched as a programmatic dependent of the one
-            // before: its blocks start as soon as SM slots free up, so a
-            // class whose queue drains early leaves its SMs to the next, and
-            // the order in which classes take the SMs is the planned one
+            // launch classes: a dependent-launch chain on the stream, or
+            // parallel branches (classes_as_chain)
+            const bool chain = classes_as_chain(b.n_work, h->sm_count);
+            if (!chain)
+                RA_CUDA(cudaEventRecord(h->fork, s));
             int qi = 0;
             for (size_t ci = 0; ci < b.classes.size(); ++ci) {
                 auto &cl = b.classes[ci];
-                const bool dependent = ci > 0;
+                const bool dependent = chain && ci > 0;
+                cudaStream_t cs = chain ? s : h->aux[ci];
+                if (!chain)
+                    RA_CUDA(cudaStreamWaitEvent(cs, h->fork, 0));
                 StripeParams p{};
                 p.work = b.d_work + cl.first;
                 p.n_work = cl.count;
@@ -515,10 +518,14 @@ int record_part(rawalign_dtw *h, Batch &b, int part, uint32_t &launches)
                 p.n_keys = (int)(b.anchored ? b.n_work : b.n_reads);
                 p.stall_handoff = h->cfg.test_stall_handoff;
                 if (cl.split)
-                    RA_CUDA(launch_split(cl.HR, p, cl.grid, s, dependent));
+                    RA_CUDA(launch_split(cl.HR, p, cl.grid, cs, dependent));
                 else
-                    RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, s, dependent));
+                    RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs, dependent));
                 ++launches;
+                if (!chain) {
+                    RA_CUDA(cudaEventRecord(h->join[ci], cs));
+                    RA_CUDA(cudaStreamWaitEvent(s, h->join[ci], 0));
+                }
             }
         }
         if (b.anchored) {
@@ -669,7 +676,15 @@ extern "C" int rawalign_dtw_create(const rawalign_dtw_config_t *config, const fl
     h->stream = (cudaStream_t)config->cuda_stream;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
-    if (cudaStreamCreateWithFlags(&h->upload, cudaStreamNonBlocking) != cudaSuccess ||
+    for (int v = 0; v < kMaxClasses; ++v) {
+        if (cudaStreamCreateWithFlags(&h->aux[v], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->join[v], cudaEventDisableTiming) != cudaSuccess) {
+            delete h;
+            return RA_EDEVICE;
+        }
+    }
+    if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->upload, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->uploaded, cudaEventDisableTiming) != cudaSuccess) {
         delete h;
         return RA_EDEVICE;
@@ -947,6 +962,14 @@ extern "C" int rawalign_dtw_destroy(rawalign_dtw_t *h)
             cudaEventDestroy(tk.second.done);
     for (auto &b : h->batches)
         free_batch(h, b.second);
+    for (int v = 0; v < kMaxClasses; ++v) {
+        if (h->aux[v])
+            cudaStreamDestroy(h->aux[v]);
+        if (h->join[v])
+            cudaEventDestroy(h->join[v]);
+    }
+    if (h->fork)
+        cudaEventDestroy(h->fork);
     if (h->uploaded)
         cudaEventDestroy(h->uploaded);
     if (h->stage)

@@ -533,6 +533,8 @@ using namespace ra_host;
 struct rawalign_dtw {
     rawalign_dtw_config_t cfg{};
     cudaStream_t stream = nullptr;
+    cudaStream_t aux[kMaxClasses] = {};   // launch classes as parallel branches (see classes_as_chain)
+    cudaEvent_t fork = nullptr, join[kMaxClasses] = {};
     cudaStream_t upload = nullptr;         // batch uploads: overlap the previous batch's kernels
     cudaEvent_t uploaded = nullptr;
     char *stage = nullptr;                 // pinned host staging for planned records (grown on demand)
@@ -917,6 +919,20 @@ inline bool make_classes_binned(PlanItem *items, size_t n, std::vector<int> &ord
                 items[x].cap = ring_need(items[x].wd, kVariants[items[x].variant][0], 2);
     });
     return make_classes(items, n, order, classes, scr, longest_first);
+}
+
+// How a run's launch classes share the GPU.  With many alignments per
+// resident group they queue as a programmatic dependent-launch chain on the
+// stream, in the plan's order (longest class first): each class's blocks
+// start as SM slots free up, and the order in which classes take the SMs is
+// the planned one (measured on GB300: anchor-guided batches 21 -> 16.6 ms and
+// steady, batched uneven 1.4 % faster).  With few alignments per group (long
+// reads) every class should start at once, so they run as parallel branches
+// on streams of their own (the chain measured 8-10 % slower on 4,000 long
+// reads).
+inline bool classes_as_chain(uint64_t n_work, int sm_count)
+{
+    return n_work >= 4ull * 32 * (uint64_t)std::max(sm_count, 1);
 }
 
 // Ring entries one piece needs: the stripe period plus two (written one step

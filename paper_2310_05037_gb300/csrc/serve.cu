@@ -825,10 +825,16 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
     RA_CUDA(launch_serve_expand((const ServeChunkDev *)(d_in + o_ch), (int)n_pend, h->arena.base,
                                 (const int *)(d_in + o_map), (const int *)(d_in + o_base), (int *)(d_in + o_fill),
                                 d_work, d_read_of, s));
-    // launch classes one after another on the stream, each a programmatic
-    // dependent of the one before (its blocks start as SM slots free up)
+    // launch classes: a dependent-launch chain on the stream, or parallel
+    // branches (classes_as_chain)
+    const bool chain = classes_as_chain(n_items, h->sm_count);
+    if (!chain)
+        RA_CUDA(cudaEventRecord(h->fork, s));
     for (int ci = 0; ci < n_classes; ++ci) {
         auto &cl = classes[ci];
+        cudaStream_t cs = chain ? s : h->aux[ci];
+        if (!chain)
+            RA_CUDA(cudaStreamWaitEvent(cs, h->fork, 0));
         StripeParams p{};
         p.work = d_work + cl.first;
         p.n_work = cl.count;
@@ -850,7 +856,11 @@ int flush_impl(rawalign_dtw *h, ServeState *st)
         p.n_fstore = h->arena.size / sizeof(float);
         p.n_results = (int)n_items;
         p.n_keys = (int)chunk_idx;
-        RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, s, ci > 0));
+        RA_CUDA(launch_stripe(cl.G, cl.HR, p, cl.grid, kBlock, cl.smem, cs, chain && ci > 0));
+        if (!chain) {
+            RA_CUDA(cudaEventRecord(h->join[ci], cs));
+            RA_CUDA(cudaStreamWaitEvent(s, h->join[ci], 0));
+        }
     }
     RA_CUDA(launch_decide(f->d_res, (int)n_items, d_keys, d_read_of, h->cfg.score_threshold, 0, s));
     RA_CUDA(cudaEventRecord(f->t_ev[2], s));
