@@ -531,14 +531,20 @@ def main():
     if not args.no_serve and rank == 0:
         from paper_2310_05037_gb300.serving import ServingLoop
 
-        pore_s, ref_s, rl_s, sreads = S.config_serving(n_reads=4096)
+        # 4 disjoint sets of 4096 reads from one generator: a full-size
+        # warm-up loop, then three measured loops (median by GCUPS; all three
+        # are reported)
+        pore_s, ref_s, rl_s, sreads_all = S.config_serving(n_reads=4 * 4096)
+        sets = [sreads_all[i * 4096:(i + 1) * 4096] for i in range(4)]
+        sreads = sets[0]
         als = B.Aligner(pore_s, ref_s, rl_s, arena_bytes=(len(ref_s) + (1536 << 20)), serve_slots=1024,
                         serve_max_events=4000, max_candidates=32, device="cuda:%d" % local,
                         serve_early_reject=True)
-        loop = ServingLoop(als, sreads[:64])
-        loop.run(max_chunks=300, in_flight=64)  # warm-up
-        loop = ServingLoop(als, sreads)
-        closed = loop.run(max_chunks=args.serve_chunks, in_flight=512).summary()
+        ServingLoop(als, sets[3]).run(max_chunks=args.serve_chunks, in_flight=512)  # warm-up
+        reps = [ServingLoop(als, sets[i]).run(max_chunks=args.serve_chunks, in_flight=512).summary()
+                for i in range(3)]
+        closed = dict(sorted(reps, key=lambda x: x["gcups"])[1])
+        closed["repeats_gcups"] = [round(x["gcups"], 1) for x in reps]
         rt = ServingLoop(als, sreads[::-1]).run(max_chunks=10 ** 9, in_flight=512, realtime=True, chunk_s=0.4,
                                                  duration_s=args.serve_realtime_s, arrival_rate=1280.0).summary()
         from paper_2310_05037_gb300.serving import collect_trajectories, decision_study
@@ -566,7 +572,8 @@ def main():
                                                         "among the candidates, 50% off-target"},
                          "workload": "Read-Until serving: Poisson stream, 512 reads in flight, 180-event chunks, "
                                      "<= 4000 events, 1-32 candidates, band 64, FREE end, 50% off-target reads",
-                         "loop": "closed loop: two generations of 256 reads, one submit_chunks + flush + "
+                         "loop": "closed loop, median of 3 runs on disjoint 4096-read sets after a full warm-up run: "
+                                 "two generations of 256 reads, one submit_chunks + flush + "
                                  "poll_chunks per generation; reads stop at the library's decision (MAPPED, or "
                                  "UNMAPPED once no candidate can reach the threshold within 4000 events)"}
         out["speedup_served_vs_plain"] = (round(closed["gcups"] / out["plain_kernel"]["gcups"], 1)

@@ -33,7 +33,8 @@
 // (the population count of each step's mask).  The stripe change, which each
 // lane makes alone while the rest of its warp waits, loads the lane's events
 // and finds its last column in O(1).
-// The cell itself is sub, min3 (one exact 3-input min), add, in that order.
+// The cell itself is sub, min3 (one exact 3-input min), add, in that order;
+// the subtractions of two rows issue as one packed f32x2 addition of -r.
 #pragma once
 
 #include <climits>
@@ -94,12 +95,17 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
     const float *rr = p.r_all;
     int m = 1, s = 0, s_end = 0;
     int k = 0, j = 0, b = INT_MAX;
-    float e[HR], D[HR];
+    // events in pairs: one packed subtraction (two f32 lanes, each rounded
+    // as a scalar subtraction) gives two rows' e - r
+    static_assert(HR % 2 == 0, "events are held in pairs");
+    float2 ep[HR / 2];
+    float D[HR];
 #pragma unroll
-    for (int r = 0; r < HR; ++r) {
-        e[r] = 0.f;
+    for (int r = 0; r < HR; ++r)
         D[r] = kInf;
-    }
+#pragma unroll
+    for (int q = 0; q < HR / 2; ++q)
+        ep[q] = make_float2(0.f, 0.f);
     // column-wise DDA: rows in band at column j are [Aq, Bq] relative to
     // the lane's first row.  Only Bq (floor, remainder Br) is stepped: both
     // edges advance by the same (cq, cr) per column, so the lower edge is the
@@ -138,12 +144,13 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         const float *evp = ev + i0;
         if (nvalid == HR) {
 #pragma unroll
-            for (int r = 0; r < HR; ++r)
-                e[r] = __ldg(evp + r);
+            for (int q = 0; q < HR / 2; ++q)
+                ep[q] = make_float2(__ldg(evp + 2 * q), __ldg(evp + 2 * q + 1));
         } else {
 #pragma unroll
-            for (int r = 0; r < HR; ++r)
-                e[r] = (r < nvalid) ? __ldg(evp + r) : kInf;
+            for (int q = 0; q < HR / 2; ++q)
+                ep[q] = make_float2((2 * q < nvalid) ? __ldg(evp + 2 * q) : kInf,
+                                    (2 * q + 1 < nvalid) ? __ldg(evp + 2 * q + 1) : kInf);
         }
         // the lane leaves the stripe after the band end of its last row
         // (clamped to the table); a full stripe's last row is HR - 1 rows
@@ -348,10 +355,15 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         rjn2 = __ldg(rr + min((unsigned)(j + 2), (unsigned)(m - 1)));
         const unsigned M = band_mask();
         float nn = upv, nw = diag, fv = kInf;
+        const float2 nrj = make_float2(-rj, -rj);
+        float2 t2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < HR; ++r) {
-            const float eg = ((M >> r) & 1u) ? e[r] : kInf;
-            const float v = __fadd_rn(fabsf(__fsub_rn(eg, rj)), min3f(nw, nn, D[r]));
+            // e - r (x + (-y) is x - y exactly), then +inf out of band
+            if ((r & 1) == 0)
+                t2 = __fadd2_rn(ep[r / 2], nrj);
+            const float dt = ((M >> r) & 1u) ? ((r & 1) ? t2.y : t2.x) : kInf;
+            const float v = __fadd_rn(fabsf(dt), min3f(nw, nn, D[r]));
             nw = D[r];
             D[r] = v;
             nn = v;
@@ -392,14 +404,20 @@ __global__ void __launch_bounds__(128) dtw_stripe_kernel(const StripeParams p)
         rjn = __ldg(rr + min((unsigned)(j + 1), (unsigned)(m - 1)));
         rjn2 = __ldg(rr + min((unsigned)(j + 2), (unsigned)(m - 1)));
         float nnA = upvA, nwA = diag, nnB = upvB, nwB = upvA, fvA = kInf, fvB = kInf;
+        const float2 nrjA = make_float2(-rjA, -rjA), nrjB = make_float2(-rjB, -rjB);
+        float2 tA2 = make_float2(0.f, 0.f), tB2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int r = 0; r < HR; ++r) {
-            const float egA = ((MA >> r) & 1u) ? e[r] : kInf;
-            const float egB = ((MB >> r) & 1u) ? e[r] : kInf;
-            const float vA = __fadd_rn(fabsf(__fsub_rn(egA, rjA)), min3f(nwA, nnA, D[r]));
+            if ((r & 1) == 0) {
+                tA2 = __fadd2_rn(ep[r / 2], nrjA);
+                tB2 = __fadd2_rn(ep[r / 2], nrjB);
+            }
+            const float dA = ((MA >> r) & 1u) ? ((r & 1) ? tA2.y : tA2.x) : kInf;
+            const float dB = ((MB >> r) & 1u) ? ((r & 1) ? tB2.y : tB2.x) : kInf;
+            const float vA = __fadd_rn(fabsf(dA), min3f(nwA, nnA, D[r]));
             nwA = D[r];
             nnA = vA;
-            const float vB = __fadd_rn(fabsf(__fsub_rn(egB, rjB)), min3f(nwB, nnB, vA));
+            const float vB = __fadd_rn(fabsf(dB), min3f(nwB, nnB, vA));
             nwB = vA;
             nnB = vB;
             D[r] = vB;
