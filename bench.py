@@ -67,7 +67,7 @@ OPS_PER_CELL = 4  # sub, min, min, add per DP cell
 ALU_SLOTS_PER_CELL = 3.6
 # DRAM bytes (read + write) of the DTW part of one step of a workload, from an
 # ncu capture of the current kernel (None: not captured for this kernel).
-TRAFFIC = {"batched": 911094272}
+TRAFFIC = {"batched": 907394816}
 TRAFFIC_BASIS = ("dram__bytes_read.sum + dram__bytes_write.sum of the striped kernel's 8 launches of one step of "
                  "the full 20k-read batch (ncu, one pass per launch, averaged over 5 replays); algorithmic bytes "
                  "per step are about 190 MB (events once, 2-bit reference once, 32 B per alignment)")
