@@ -361,6 +361,121 @@ inline Sched schedule(const BandDef &b, int64_t row0, int64_t nrows, int G, int 
     return s;
 }
 
+// ---------------------------------------------------------------- flat map
+// Hash map from 64-bit keys (tickets, read ids) to small values, for the
+// serving path's per-chunk bookkeeping: open addressing with linear probing
+// in one array (no allocation per entry), at most half full, and deletion by
+// backward shift (no tombstones, so lookups stay short however many entries
+// come and go).  Every key value is allowed; occupancy is kept apart.
+template <class V>
+class FlatMap64 {
+  public:
+    explicit FlatMap64(size_t cap = 16) { rehash(cap); }
+    size_t size() const { return n_; }
+    void reserve(size_t n)
+    {
+        if (2 * n > keys_.size())
+            rehash(2 * n);
+    }
+    void clear()
+    {
+        if (n_)
+            std::fill(used_.begin(), used_.end(), (uint8_t)0);
+        n_ = 0;
+    }
+    V *find(uint64_t k)
+    {
+        for (size_t i = slot(k);; i = (i + 1) & mask_) {
+            if (!used_[i])
+                return nullptr;
+            if (keys_[i] == k)
+                return &vals_[i];
+        }
+    }
+    bool contains(uint64_t k) { return find(k) != nullptr; }
+    // the value of k, inserted value-initialised when absent
+    V &operator[](uint64_t k)
+    {
+        if (V *v = find(k))
+            return *v;
+        if (2 * (n_ + 1) > keys_.size())
+            rehash(2 * keys_.size());
+        size_t i = slot(k);
+        while (used_[i])
+            i = (i + 1) & mask_;
+        used_[i] = 1;
+        keys_[i] = k;
+        vals_[i] = V();
+        ++n_;
+        return vals_[i];
+    }
+    bool erase(uint64_t k)
+    {
+        size_t i = slot(k);
+        while (true) {
+            if (!used_[i])
+                return false;
+            if (keys_[i] == k)
+                break;
+            i = (i + 1) & mask_;
+        }
+        // backward shift: move later entries of the probe run into the hole
+        // unless their home slot lies cyclically in (hole, entry]
+        size_t j = i;
+        while (true) {
+            j = (j + 1) & mask_;
+            if (!used_[j])
+                break;
+            const size_t h = slot(keys_[j]);
+            const bool stays = (i <= j) ? (i < h && h <= j) : (i < h || h <= j);
+            if (stays)
+                continue;
+            keys_[i] = keys_[j];
+            vals_[i] = vals_[j];
+            i = j;
+        }
+        used_[i] = 0;
+        --n_;
+        return true;
+    }
+
+  private:
+    // the finaliser of MurmurHash3 (a bijective 64-bit mix)
+    size_t slot(uint64_t k) const
+    {
+        k ^= k >> 33;
+        k *= 0xff51afd7ed558ccdull;
+        k ^= k >> 33;
+        k *= 0xc4ceb9fe1a85ec53ull;
+        k ^= k >> 33;
+        return (size_t)k & mask_;
+    }
+    void rehash(size_t cap)
+    {
+        size_t c = 16;
+        while (c < cap)
+            c <<= 1;
+        std::vector<uint64_t> ok;
+        std::vector<V> ov;
+        std::vector<uint8_t> ou;
+        ok.swap(keys_);
+        ov.swap(vals_);
+        ou.swap(used_);
+        keys_.assign(c, 0);
+        vals_.assign(c, V());
+        used_.assign(c, 0);
+        mask_ = c - 1;
+        n_ = 0;
+        for (size_t x = 0; x < ou.size(); ++x)
+            if (ou[x])
+                (*this)[ok[x]] = ov[x];
+    }
+    std::vector<uint64_t> keys_;
+    std::vector<V> vals_;
+    std::vector<uint8_t> used_;
+    size_t mask_ = 0, n_ = 0;
+};
+
 // ---------------------------------------------------------------- arena
 // Best-fit allocator over the caller's arena: free ranges indexed by offset
 // (to merge a released range with its neighbours) and by size (to find the

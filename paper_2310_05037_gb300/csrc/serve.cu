@@ -124,7 +124,7 @@ struct ServeState {
     std::vector<PendingChunk> pending;  // [0, n_pending) are queued; later entries keep their buffers for reuse
     size_t n_pending = 0;
     std::map<uint64_t, FlushRec *> flushes;       // by flush id
-    std::unordered_map<uint64_t, uint64_t> ticket_flush;  // ticket -> flush id
+    FlatMap64<uint64_t> ticket_flush;  // ticket -> flush id
     // reaped results: one block per flush, and per ticket its place in the block
     struct ReadyBlock {
         std::vector<rawalign_result_t> res;
@@ -135,7 +135,7 @@ struct ServeState {
         uint32_t first, count;
     };
     std::unordered_map<uint64_t, ReadyBlock> ready_blocks;  // by flush id
-    std::unordered_map<uint64_t, ReadyRef> ready;           // by ticket
+    FlatMap64<ReadyRef> ready;                              // by ticket
     std::vector<std::vector<rawalign_result_t>> res_pool;   // result buffers of polled blocks, for reuse
     void drop_block(std::unordered_map<uint64_t, ReadyBlock>::iterator b)
     {
@@ -155,7 +155,7 @@ struct ServeState {
         std::vector<int> cls_count, cls_map, cls_base;
         std::vector<ClassLaunch> classes;
     } scratch;
-    std::unordered_map<uint64_t, size_t> pending_at;           // read id -> index in pending
+    FlatMap64<size_t> pending_at;                              // read id -> index in pending
     uint64_t next_flush = 1;
     PinnedPool pinned;
     std::vector<cudaEvent_t> timing_events;  // reusable timing events
@@ -317,11 +317,13 @@ void serve_destroy(rawalign_dtw *h)
 
 // Copies up to cap results of a reaped ticket into out and forgets the
 // ticket (and its flush's block once every ticket of the flush is taken).
-uint32_t take_ready(ServeState *st, std::unordered_map<uint64_t, ServeState::ReadyRef>::iterator r,
-                    rawalign_result_t *out, uint32_t cap)
+uint32_t take_ready(ServeState *st, uint64_t ticket, rawalign_result_t *out, uint32_t cap)
 {
-    const ServeState::ReadyRef ref = r->second;
-    st->ready.erase(r);
+    const ServeState::ReadyRef *r = st->ready.find(ticket);
+    if (!r)
+        return 0;
+    const ServeState::ReadyRef ref = *r;
+    st->ready.erase(ticket);
     auto b = st->ready_blocks.find(ref.fid);
     if (b == st->ready_blocks.end())
         return 0;
@@ -340,10 +342,9 @@ int serve_poll(rawalign_dtw *h, uint64_t ticket, rawalign_result_t *out, uint32_
     ServeState *st = h->serve;
     if (!st)
         return RA_OK;
-    auto r = st->ready.find(ticket);
-    if (r == st->ready.end()) {
-        auto tf = st->ticket_flush.find(ticket);
-        if (tf == st->ticket_flush.end()) {
+    if (!st->ready.contains(ticket)) {
+        const uint64_t *tf = st->ticket_flush.find(ticket);
+        if (!tf) {
             // queued but not flushed yet?
             for (size_t ci = 0; ci < st->n_pending; ++ci)
                 for (uint64_t t : st->pending[ci].tickets)
@@ -354,7 +355,8 @@ int serve_poll(rawalign_dtw *h, uint64_t ticket, rawalign_result_t *out, uint32_
             return RA_OK;  // not a serving ticket
         }
         *handled = true;
-        FlushRec *f = st->flushes[tf->second];
+        const uint64_t fid = *tf;
+        FlushRec *f = st->flushes[fid];
         auto t0 = std::chrono::steady_clock::now();
         while (true) {
             cudaError_t e = cudaEventQuery(f->done);
@@ -371,13 +373,12 @@ int serve_poll(rawalign_dtw *h, uint64_t ticket, rawalign_result_t *out, uint32_
             }
             std::this_thread::sleep_for(std::chrono::microseconds(10));
         }
-        reap(h, st, tf->second, f);
-        r = st->ready.find(ticket);
-        if (r == st->ready.end())
+        reap(h, st, fid, f);
+        if (!st->ready.contains(ticket))
             return RA_EDEVICE;
     }
     *handled = true;
-    *n_out = take_ready(st, r, out, cap);
+    *n_out = take_ready(st, ticket, out, cap);
     return RA_OK;
 }
 
@@ -388,12 +389,24 @@ namespace {
 
 // Queues one chunk (the body of rawalign_dtw_submit_chunk); nothing changes
 // when it returns an error.
+// No NaN or infinity among x[0, n): an exponent field of all ones, tested
+// without an early exit so that the host compiler vectorises the loop.
+bool all_finite(const float *x, uint32_t n)
+{
+    uint32_t bad = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t u;
+        memcpy(&u, x + i, sizeof u);
+        bad |= (uint32_t)((u & 0x7f800000u) == 0x7f800000u);
+    }
+    return bad == 0;
+}
+
 int submit_one(rawalign_dtw *h, ServeState *st, uint64_t read_id, const float *events, uint32_t n_events,
                const rawalign_candidate_t *cands, uint32_t n_cands, int last, uint64_t *ticket)
 {
-    for (uint32_t x = 0; x < n_events; ++x)
-        if (!std::isfinite(events[x]))
-            return RA_EINVAL;
+    if (!all_finite(events, n_events))
+        return RA_EINVAL;
     auto it = st->reads.find(read_id);
     if (it == st->reads.end()) {
         // admission: a read slot and arena memory for the read's device state
@@ -460,9 +473,8 @@ int submit_one(rawalign_dtw *h, ServeState *st, uint64_t read_id, const float *e
         return RA_EINVAL;
     // one pending chunk per read per flush: later chunks join it
     PendingChunk *pc = nullptr;
-    auto pa = st->pending_at.find(read_id);
-    if (pa != st->pending_at.end())
-        pc = &st->pending[pa->second];
+    if (const size_t *pa = st->pending_at.find(read_id))
+        pc = &st->pending[*pa];
     uint64_t queued = pc ? pc->ev.size() : 0;
     if (st->max_events && rd.rows_done + queued + n_events > st->max_events)
         return RA_EINVAL;
@@ -912,11 +924,10 @@ extern "C" int rawalign_dtw_poll_chunks(rawalign_dtw_t *h, const uint64_t *ticke
     std::vector<uint64_t> wait_for;
     for (uint32_t x = 0; x < n_tickets; ++x) {
         const uint64_t t = tickets[x];
-        if (st->ready.count(t))
+        if (st->ready.contains(t))
             continue;
-        auto tf = st->ticket_flush.find(t);
-        if (tf != st->ticket_flush.end()) {
-            wait_for.push_back(tf->second);
+        if (const uint64_t *tf = st->ticket_flush.find(t)) {
+            wait_for.push_back(*tf);
             continue;
         }
         for (size_t ci = 0; ci < st->n_pending; ++ci)
@@ -954,16 +965,16 @@ extern "C" int rawalign_dtw_poll_chunks(rawalign_dtw_t *h, const uint64_t *ticke
     }
     uint64_t total = 0;
     for (uint32_t x = 0; x < n_tickets; ++x) {
-        auto r = st->ready.find(tickets[x]);
-        if (r == st->ready.end())
+        const ServeState::ReadyRef *r = st->ready.find(tickets[x]);
+        if (!r)
             return RA_EDEVICE;
-        total += r->second.count;
+        total += r->count;
     }
     if (total > cap)
         return RA_EINVAL;
     uint64_t pos = 0;
     for (uint32_t x = 0; x < n_tickets; ++x) {
-        const uint32_t n = take_ready(st, st->ready.find(tickets[x]), out + pos, UINT32_MAX);
+        const uint32_t n = take_ready(st, tickets[x], out + pos, UINT32_MAX);
         counts[x] = n;
         pos += n;
     }

@@ -17,7 +17,8 @@
 // classes ordered by their longest alignment; and the O(1) row step of the
 // band DDA (ra::row_dda, used by the kernel at every stripe change) against
 // stepping row by row; and that the planner's parallel loops visit every
-// index once, with concurrent and nested callers.
+// index once, with concurrent and nested callers; and the serving path's flat
+// hash map (FlatMap64) against std::unordered_map.
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
@@ -26,6 +27,7 @@
 #include <numeric>
 #include <random>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "engine.h"
@@ -441,6 +443,57 @@ int main()
         for (auto &kv : live)
             ar.release((char *)0x10000 + kv.first);
         CHECK(ar.alloc(kArena) != nullptr, "released arena does not merge back into one range\n");
+    }
+    // the serving path's flat hash map against std::unordered_map: random
+    // inserts, lookups and erases (backward-shift deletion across the
+    // array's wrap-around), keys from a small range (long probe runs), from
+    // the whole 64-bit range (0 and ~0 included) and sequential (tickets),
+    // with growth from the smallest size and clear()
+    {
+        for (int mode = 0; mode < 3; ++mode) {
+            FlatMap64<uint64_t> fm;
+            std::unordered_map<uint64_t, uint64_t> ref;
+            uint64_t seq = 1;
+            auto key = [&]() -> uint64_t {
+                if (mode == 0)
+                    return rng() % 512;
+                if (mode == 1) {
+                    const uint64_t k = ((uint64_t)rng() << 32) ^ rng();
+                    return rng() % 16 == 0 ? (rng() % 2 ? 0ull : ~0ull) : k;
+                }
+                return rng() % 4 ? seq++ : seq - 1 - rng() % std::min<uint64_t>(seq, 300);
+            };
+            for (int op = 0; op < 300000; ++op) {
+                const uint64_t k = key();
+                const unsigned r = rng() % 10;
+                if (r < 4) {
+                    const uint64_t v = rng();
+                    fm[k] = v;
+                    ref[k] = v;
+                } else if (r < 7) {
+                    CHECK(fm.erase(k) == (ref.erase(k) == 1), "flat map erase disagrees (key %llu)\n",
+                          (unsigned long long)k);
+                } else {
+                    const uint64_t *v = fm.find(k);
+                    auto it = ref.find(k);
+                    CHECK((v != nullptr) == (it != ref.end()) && (!v || *v == it->second),
+                          "flat map lookup disagrees (key %llu)\n", (unsigned long long)k);
+                }
+                if (op % 50000 == 49999) {
+                    for (auto &kv : ref) {
+                        const uint64_t *v = fm.find(kv.first);
+                        CHECK(v && *v == kv.second, "flat map lost a key\n");
+                    }
+                    CHECK(fm.size() == ref.size(), "flat map size %zu, expected %zu\n", fm.size(), ref.size());
+                }
+                if (op == 150000) {
+                    fm.clear();
+                    ref.clear();
+                    CHECK(fm.size() == 0 && !fm.contains(k), "flat map clear\n");
+                }
+                ++cases;
+            }
+        }
     }
     printf("cases %llu steps %llu fails %d\n", (unsigned long long)cases, (unsigned long long)steps, fails);
     return fails ? 1 : 0;
