@@ -111,6 +111,8 @@ class ServingLoop:
         ready_at = np.zeros(n, np.float64)     # when the read's next chunk may go
         live = np.zeros(n, bool)               # admitted and not decided
         busy = np.zeros(n, bool)               # a chunk in flight
+        idle = np.zeros(n, bool)               # live and not busy (kept with live and busy)
+        n_live = 0
         pending = collections.deque(range(n))  # reads not admitted yet
         to_close = []                          # reads decided early, still open in the library
         gens = collections.deque()             # (tickets, reads, t_submit, closing tickets)
@@ -127,11 +129,10 @@ class ServingLoop:
                 break
             if st.chunks >= max_chunks:
                 break
-            if not pending and not live.any() and not gens and not to_close:
+            if not pending and n_live == 0 and not gens and not to_close:
                 break
             # admission: closed loop keeps in_flight reads live, real time
             # admits Poisson arrivals
-            n_live = int(live.sum())
             newq = []
             while pending and n_live + len(newq) < in_flight and (not realtime or now >= next_arrival):
                 newq.append(pending.popleft())
@@ -140,46 +141,60 @@ class ServingLoop:
             if newq:
                 newq = np.array(newq, np.int64)
                 live[newq] = True
+                idle[newq] = True
+                n_live += len(newq)
                 ready_at[newq] = now
             # the reads whose next chunk can go now: in closed loop at most one
             # generation's worth, and only while fewer generations are in flight
-            q = np.nonzero(live & ~busy & (ready_at <= now))[0]
-            if not realtime:
-                q = q[:gen_cap] if len(gens) < generations else q[:0]
+            if realtime:
+                q = np.flatnonzero(idle & (ready_at <= now))
+            elif len(gens) < generations:
+                q = np.flatnonzero(idle)[:gen_cap]
+            else:
+                q = np.zeros(0, np.int64)
             closes = np.array(to_close, np.int64)
             to_close = []
             if len(q) or len(closes):
                 t_start = time.perf_counter()  # a chunk's latency runs from here to its result on the host
-                ch = np.concatenate([self._chunks(q, pos[q], False), self._chunks(closes, pos[closes], True)])
+                ch = self._chunks(q, pos[q], False)
+                if len(closes):
+                    ch = np.concatenate([ch, self._chunks(closes, pos[closes], True)])
                 a = time.perf_counter()
                 tickets, status = B.rawalign_dtw_submit_chunks(h, ch, self.events, self.cands)
                 t_sub += time.perf_counter() - a
                 sq = status[: len(q)]
-                bad = np.concatenate([sq[(sq != B.RA_OK) & (sq != B.RA_EAGAIN)], status[len(q):][status[len(q):] != 0]])
-                if len(bad):
-                    raise B.RawAlignError("rawalign_dtw_submit_chunks", int(bad[0]))
-                # reads refused admission (no slot or arena memory) wait in front
-                refused = q[sq == B.RA_EAGAIN]
-                live[refused] = False
-                pending.extendleft(reversed(refused.tolist()))
                 ok = sq == B.RA_OK
-                qs = q[ok]
+                if not ok.all() or status[len(q):].any():
+                    bad = np.concatenate([sq[~ok & (sq != B.RA_EAGAIN)], status[len(q):][status[len(q):] != 0]])
+                    if len(bad):
+                        raise B.RawAlignError("rawalign_dtw_submit_chunks", int(bad[0]))
+                    # reads refused admission (no slot or arena memory) wait in front
+                    refused = q[sq == B.RA_EAGAIN]
+                    live[refused] = False
+                    n_live -= len(refused)
+                    pending.extendleft(reversed(refused.tolist()))
+                    qs = q[ok]
+                    pos[qs] += ch["n_events"][: len(q)][ok].astype(np.int64)
+                else:
+                    qs = q
+                    pos[qs] += ch["n_events"][: len(q)].astype(np.int64)
+                idle[q] = False
                 busy[qs] = True
-                pos[qs] += ch["n_events"][: len(q)][ok].astype(np.int64)
                 a = time.perf_counter()
                 B.rawalign_dtw_flush(h)
                 t_flush += time.perf_counter() - a
                 st.flushes += 1
-                gens.append((tickets[: len(q)][ok], qs, t_start, tickets[len(q):]))
+                gens.append((tickets[: len(q)][ok] if len(qs) < len(q) else tickets[: len(q)], qs, t_start,
+                             tickets[len(q):]))
             # read back the oldest generation: in closed loop when the others
             # are on the GPU (or nothing else can start), in real time as soon
             # as it has completed
             while gens:
                 tk, qs, ts, ctk = gens[0]
-                must = (not realtime) and (len(gens) >= generations or not np.any(live & ~busy))
+                must = (not realtime) and (len(gens) >= generations or not idle.any())
                 a = time.perf_counter()
-                got = B.rawalign_dtw_poll_chunks(h, np.concatenate([tk, ctk]), int(self.n_cand[qs].sum()) + 1,
-                                                 timeout_us=-1 if must else 0)
+                got = B.rawalign_dtw_poll_chunks(h, np.concatenate([tk, ctk]) if len(ctk) else tk,
+                                                 int(self.n_cand[qs].sum()) + 1, timeout_us=-1 if must else 0)
                 t_poll += time.perf_counter() - a
                 if got is None:
                     break
@@ -205,8 +220,11 @@ class ServingLoop:
                 st.accepted += int(acc.sum())
                 st.rejected += int(rej.sum())
                 st.exhausted += int(exh.sum())
-                st.reads_done += int(done.sum())
+                n_done = int(done.sum())
+                st.reads_done += n_done
+                n_live -= n_done
                 live[qs[done]] = False
+                idle[qs] = ~done
                 # decided before their last chunk: closed in the next round
                 to_close.extend(qs[done & ~at_end].tolist())
                 if must:
