@@ -19,9 +19,9 @@
 // ring (>= dC + 2 entries) is never overwritten before it is read.
 //
 // Band (Sec. 2.4.3): out-of-band cells must act as +inf.  Instead of masking
-// each result, the event value of a row that is outside the band at the
-// current column is replaced by +inf, so d = |e - r| = +inf and the cell is
-// +inf whatever its neighbours are; this keeps the select off the dependent
+// each result, the difference e - r of a row that is outside the band at the
+// current column is replaced by +inf, so d = +inf and the cell is +inf
+// whatever its neighbours are; this keeps the select off the dependent
 // min -> add chain.  The rows in band at column j form an interval, found
 // each step by a column-wise DDA (the last row whose band reaches j; the
 // first row whose band has started is that one less a constant) and turned
