@@ -337,9 +337,15 @@ def rawalign_dtw_serve_stats(h, reset: bool = False) -> ServeStats:
     return s
 
 
-def rawalign_dtw_poll(h, ticket: int, cap: int, timeout_us: int = -1):
-    """Returns a structured array of results, or None while RA_ENOTREADY."""
-    out = np.zeros(max(cap, 1), RESULT_DTYPE)
+def rawalign_dtw_poll(h, ticket: int, cap: int, timeout_us: int = -1, out=None):
+    """Returns a structured array of results, or None while RA_ENOTREADY.
+    out: optional RESULT_DTYPE array of at least cap records to write into
+    (e.g. a view of pinned memory reused across calls, so that the results
+    come back in one fast copy); the return value is then a view of it."""
+    if out is None:
+        out = np.zeros(max(cap, 1), RESULT_DTYPE)
+    elif out.dtype != RESULT_DTYPE or not out.flags.c_contiguous or len(out) < cap:
+        raise TypeError("out must be a contiguous RESULT_DTYPE array of at least cap records")
     n = C.c_uint32()
     code = load().rawalign_dtw_poll(h, int(ticket), _ptr(out), cap, C.byref(n), int(timeout_us))
     if code == RA_ENOTREADY:
@@ -435,8 +441,8 @@ class Aligner:
     def run(self, batch):
         return rawalign_dtw_run_batch(self.h, batch)
 
-    def poll(self, ticket, cap, timeout_us=-1):
-        return rawalign_dtw_poll(self.h, ticket, cap, timeout_us)
+    def poll(self, ticket, cap, timeout_us=-1, out=None):
+        return rawalign_dtw_poll(self.h, ticket, cap, timeout_us, out)
 
     def stats(self, batch):
         return rawalign_dtw_batch_stats(self.h, batch)

@@ -136,3 +136,15 @@ def test_missing_library_fails_loudly(tmp_path):
             B.load(str(tmp_path / "nope.so"))
     finally:
         B._lib = saved
+
+
+def test_poll_rejects_an_unusable_output_buffer():
+    """rawalign_dtw_poll(out=...) writes into the caller's array only when it
+    can hold cap records of the result layout; anything else is refused
+    before the library is called."""
+    with pytest.raises(TypeError):
+        B.rawalign_dtw_poll(None, 1, 4, out=np.zeros(4, np.float64))
+    with pytest.raises(TypeError):
+        B.rawalign_dtw_poll(None, 1, 4, out=np.zeros(3, B.RESULT_DTYPE))
+    with pytest.raises(TypeError):
+        B.rawalign_dtw_poll(None, 1, 4, out=np.zeros(8, B.RESULT_DTYPE)[::2])
