@@ -341,6 +341,13 @@ def time_e2e(B, torch, al, w, steps, world):
             t = t_next
         return r
 
+    # the host part of one submission, from a batch prepared the same way
+    # (after the handle's first prepare, which also allocates its staging)
+    bp = (al.prepare_anchored(ev_np, off_np, cand_np, w.anchors, w.anchor_offsets) if anchored
+          else al.prepare(ev_np, off_np, cand_np))
+    al.poll(al.run(bp), 0)
+    host = prepare_split(al.stats(bp))
+    al.release(bp)
     pipelined(2)
     barrier(world)
     t0 = time.perf_counter()
@@ -353,7 +360,14 @@ def time_e2e(B, torch, al, w, steps, world):
             "d2h_bytes_per_step": int(w.n_cands * B.RESULT_DTYPE.itemsize),
             "ms_per_step": round(el / steps * 1e3, 2),
             "pipelining": "two submissions in flight (submit i+1, then poll i)",
-            "host_buffers": "pinned inputs and one pinned result buffer reused every step"}
+            "host_buffers": "pinned inputs and one pinned result buffer reused every step",
+            "host_prepare_ms": host}
+
+
+def prepare_split(st):
+    """Host time of one prepare of a step's batch (the work each end-to-end
+    submission repeats): planning on the library's threads, then the uploads."""
+    return {"plan": round(st.host_plan_ms, 2), "upload": round(st.host_upload_ms, 2)}
 
 
 def peak_gcups(torch, local):

@@ -276,6 +276,10 @@ typedef struct {
     uint64_t slots;            /* lane-cell slots the plan occupies (>= cells) */
     uint32_t launches;         /* kernels launched by one run */
     uint32_t split;            /* alignments run on a block of four warps (the longest ones) */
+    double host_plan_ms;       /* host time of prepare spent planning (checks, bands, schedules,
+                                  launch classes, staging of the records), on the library's threads */
+    double host_upload_ms;     /* host time of prepare from issuing the uploads to their end
+                                  (prepare returns once its inputs are copied) */
 } rawalign_dtw_stats_t;
 int rawalign_dtw_batch_stats(rawalign_dtw_t *h, uint64_t batch, rawalign_dtw_stats_t *out);
 

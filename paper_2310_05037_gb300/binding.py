@@ -96,6 +96,8 @@ class Stats(C.Structure):
         ("slots", C.c_uint64),
         ("launches", C.c_uint32),
         ("split", C.c_uint32),
+        ("host_plan_ms", C.c_double),
+        ("host_upload_ms", C.c_double),
     ]
 
 

@@ -77,6 +77,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
                     uint32_t n_reads, const rawalign_candidate_t *cands, uint32_t n_cands,
                     const rawalign_anchor_t *anchors = nullptr, const uint64_t *anchor_offs = nullptr)
 {
+    const auto t_plan = std::chrono::steady_clock::now();
     const int k = h->cfg.k;
     b.n_reads = n_reads;
     b.n_cands = n_cands;
@@ -439,6 +440,8 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     // overlap the kernels of the batch before it; the handle's stream waits
     // for them, and the host only for the copies themselves
     cudaStream_t s = h->upload;
+    const auto t_upload = std::chrono::steady_clock::now();
+    b.host_plan_ms = std::chrono::duration<double, std::milli>(t_upload - t_plan).count();
     RA_CUDA(cudaMemcpyAsync(b.d_events, events, sizeof(float) * b.n_events, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_sig, sig, sizeof(SigDesc) * n_cands, cudaMemcpyHostToDevice, s));
     RA_CUDA(cudaMemcpyAsync(b.d_work, work, sizeof(WorkDesc) * b.n_work, cudaMemcpyHostToDevice, s));
@@ -453,6 +456,7 @@ int plan_and_upload(rawalign_dtw *h, Batch &b, const float *events, const uint64
     RA_CUDA(cudaStreamWaitEvent(h->stream, h->uploaded, 0));
     // the caller may free its buffers on return
     RA_CUDA(cudaEventSynchronize(h->uploaded));
+    b.host_upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_upload).count();
     return RA_OK;
 }
 
@@ -929,6 +933,8 @@ extern "C" int rawalign_dtw_batch_stats(rawalign_dtw_t *h, uint64_t batch, rawal
     out->split = b.n_split;
     out->slots = b.slots;
     out->launches = b.launches;
+    out->host_plan_ms = b.host_plan_ms;
+    out->host_upload_ms = b.host_upload_ms;
     return RA_OK;
 }
 

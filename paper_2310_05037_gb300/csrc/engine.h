@@ -567,6 +567,7 @@ struct Batch {
     uint64_t n_events = 0;
     uint64_t n_r = 0;            // expected values in d_r
     uint32_t n_split = 0;        // work items on the block-split kernel
+    double host_plan_ms = 0, host_upload_ms = 0;  // host time of prepare: planning, uploads
     std::vector<void *> blocks;  // arena allocations
     float *d_events = nullptr;
     SigDesc *d_sig = nullptr;

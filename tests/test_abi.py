@@ -62,6 +62,7 @@ int main(void) {
   O(rawalign_chunk_t, cand_offset); O(rawalign_chunk_t, n_cands); O(rawalign_chunk_t, last);
   O(rawalign_dtw_serve_stats_t, cells); O(rawalign_dtw_serve_stats_t, host_submit_ms);
   O(rawalign_dtw_serve_stats_t, d2h_ms);
+  O(rawalign_dtw_stats_t, split); O(rawalign_dtw_stats_t, host_plan_ms); O(rawalign_dtw_stats_t, host_upload_ms);
   O(rawalign_anchor_t, q); O(rawalign_anchor_t, t); O(rawalign_anchor_t, len);
   O(rawalign_candidate_t, read_id); O(rawalign_candidate_t, ref_offset); O(rawalign_candidate_t, ref_len_bases);
   O(rawalign_candidate_t, strand); O(rawalign_candidate_t, band_w); O(rawalign_candidate_t, slope_num);
@@ -105,6 +106,9 @@ def test_record_layouts_agree():
             continue
         if T == "rawalign_dtw_serve_stats_t":
             assert getattr(B.ServeStats, f).offset == int(v), k
+            continue
+        if T == "rawalign_dtw_stats_t":
+            assert getattr(B.Stats, f).offset == int(v), k
             continue
         py = {"rawalign_candidate_t": B.Candidate, "rawalign_result_t": B.Result, "rawalign_dtw_config_t": B.Config}[T]
         assert getattr(py, f).offset == int(v), k
