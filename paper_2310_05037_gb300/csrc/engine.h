@@ -16,6 +16,8 @@
 #include <new>
 #include <set>
 #include <thread>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -44,8 +46,8 @@ constexpr int kLag = ra::kLaneLag;  // columns between neighbouring lanes (the k
 // measurement on a GB300 (each variant on a batch shaped for its steady
 // state; 8 rows per lane pay the per-step overhead over fewer cells, 24 rows
 // amortise it further).  rawalign_dtw_set_variant_costs replaces them.
-const int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}, {16, 24}, {8, 24}, {32, 24},
-                           {4, 24}};
+constexpr int kVariants[][2] = {{32, 16}, {16, 16}, {32, 8}, {16, 8}, {8, 8}, {4, 8}, {16, 24}, {8, 24}, {32, 24},
+                               {4, 24}};
 const double kSlotCost[] = {1.2107, 1.2336, 1.8882, 1.9132, 1.9968, 2.1240, 1.0095, 1.0287, 1.0, 1.0656};
 constexpr int kNumVariants = 10;
 constexpr int kSplitVariant = 8;  // (32, 24): the lane layout of the block-split kernel
@@ -334,6 +336,35 @@ struct Sched {
     double cells_est = 0;
     double eff = 0;  // in-band cells / lane-cell slots (estimate)
 };
+
+// The part of schedule() that depends on the variant, given the band edges
+// every variant shares (a0 = lo(row0), b_last = hi(last row)); with G and HR
+// fixed at compile time the divisions by H and HR become multiplications.
+// Same operations in the same order as schedule(), so the same results.
+template <int G, int HR>
+inline Sched schedule_from_edges(const BandDef &b, int64_t nrows, int64_t a0, int64_t b_last)
+{
+    Sched s;
+    constexpr int64_t H = (int64_t)G * HR;
+    const int64_t K = (nrows + H - 1) / H;
+    s.a0 = (int32_t)a0;
+    if (s.a0 > b.m - 1) {
+        s.s_end = 0;
+        return s;
+    }
+    int64_t span = fdiv(2 * b.w * b.den - (H - HR + 1) * b.num, b.den);
+    span = std::min<int64_t>(span, b.m - 1);
+    const int64_t dC = std::max<int64_t>((int64_t)kLag * G + 3, span + 2);
+    const int64_t nl = nrows - 1 - (K - 1) * H;
+    const int64_t t_last = nl / HR;
+    s.dC = (int32_t)dC;
+    const int64_t se = b_last - s.a0 + 3 + (int64_t)kLag * t_last + (K - 1) * dC;
+    s.s_end = (int32_t)std::max<int64_t>(se, 1);
+    s.cells_est = (double)nrows * (double)std::min<int64_t>(2 * b.w + 1, b.m);
+    const double slots = (double)s.s_end * G * HR;
+    s.eff = slots > 0 ? s.cells_est / slots : 0;
+    return s;
+}
 
 inline Sched schedule(const BandDef &b, int64_t row0, int64_t nrows, int G, int HR)
 {
@@ -701,24 +732,36 @@ inline int next_pow2(int64_t x)
 
 // Chooses the striped variant for one piece of an alignment: most in-band
 // cells per unit of issue cost, ties to the earlier (wider) variant.
+// f(std::integral_constant<int, v>) for v = 0, 1, ... in order
+template <class F, size_t... V>
+inline void for_each_variant(F &&f, std::index_sequence<V...>)
+{
+    (f(std::integral_constant<int, (int)V>{}), ...);
+}
+
 inline int choose_variant(const BandDef &band, int64_t row0, int64_t n, Sched &out, const double *cost = kSlotCost)
 {
+    // the band edges of the first and last rows are the same for every
+    // variant: computed once, then each variant's schedule from them
+    const int64_t a0 = band.lo(row0), b_last = band.hi(row0 + n - 1);
+    if (a0 > band.m - 1) {
+        // no cell in the first row: nothing to schedule (every variant agrees)
+        out = schedule_from_edges<kVariants[0][0], kVariants[0][1]>(band, n, a0, b_last);
+        return 0;
+    }
     int best = -1;
     double best_score = -1;
-    for (int v = 0; v < kNumVariants; ++v) {
-        const int G = kVariants[v][0], HR = kVariants[v][1];
-        Sched s = schedule(band, row0, n, G, HR);
-        if (s.s_end <= 0) {
-            out = s;
-            return 0;
-        }
+    auto consider = [&](auto vt) {
+        constexpr int v = decltype(vt)::value;
+        const Sched s = schedule_from_edges<kVariants[v][0], kVariants[v][1]>(band, n, a0, b_last);
         const double score = s.eff / cost[v] * (1.0 + 0.02 * (kNumVariants - v));
         if (score > best_score) {
             best_score = score;
             best = v;
             out = s;
         }
-    }
+    };
+    for_each_variant(consider, std::make_index_sequence<kNumVariants>{});
     return best;
 }
 

@@ -17,8 +17,9 @@
 // classes ordered by their longest alignment; and the O(1) row step of the
 // band DDA (ra::row_dda, used by the kernel at every stripe change) against
 // stepping row by row; and that the planner's parallel loops visit every
-// index once, with concurrent and nested callers; and the serving path's flat
-// hash map (FlatMap64) against std::unordered_map.
+// index once, with concurrent and nested callers; choose_variant against the
+// plain loop over schedule(); and the serving path's flat hash map
+// (FlatMap64) against std::unordered_map.
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
@@ -443,6 +444,46 @@ int main()
         for (auto &kv : live)
             ar.release((char *)0x10000 + kv.first);
         CHECK(ar.alloc(kArena) != nullptr, "released arena does not merge back into one range\n");
+    }
+    // choose_variant (each variant's schedule from the shared band edges,
+    // with compile-time G and HR) against the plain loop over schedule():
+    // the same variant and the same schedule, bit for bit, for random bands,
+    // slopes, widths and first rows (serving pieces start mid-read)
+    {
+        for (int rep = 0; rep < 300000; ++rep) {
+            BandDef band;
+            int32_t wr;
+            const int64_t n = 1 + (int64_t)(rng() % 5000), m = 1 + (int64_t)(rng() % 6000);
+            const int64_t num = rng() % 3 ? (int64_t)(rng() % 7000) : 0, den = 1 + (int64_t)(rng() % 7000);
+            const int32_t bw = rng() % 3 ? (int32_t)(rng() % 400) : -1;
+            if (band_for(n + 2, m, bw, num, den, band, wr) != 0)
+                continue;
+            const int64_t row0 = rng() % 2 ? 0 : (int64_t)(rng() % 4000), rows = 1 + (int64_t)(rng() % 800);
+            Sched ref{};
+            int vref = -1;
+            double best = -1;
+            for (int v = 0; v < kNumVariants; ++v) {
+                const Sched sv = schedule(band, row0, rows, kVariants[v][0], kVariants[v][1]);
+                if (sv.s_end <= 0) {
+                    ref = sv;
+                    vref = 0;
+                    break;
+                }
+                const double score = sv.eff / kSlotCost[v] * (1.0 + 0.02 * (kNumVariants - v));
+                if (score > best) {
+                    best = score;
+                    vref = v;
+                    ref = sv;
+                }
+            }
+            Sched got{};
+            const int v = choose_variant(band, row0, rows, got);
+            CHECK(v == vref && got.dC == ref.dC && got.a0 == ref.a0 && got.s_end == ref.s_end &&
+                      got.cells_est == ref.cells_est && got.eff == ref.eff,
+                  "choose_variant differs from the loop over schedule() (n %lld m %lld row0 %lld)\n", (long long)rows,
+                  (long long)m, (long long)row0);
+            ++cases;
+        }
     }
     // the serving path's flat hash map against std::unordered_map: random
     // inserts, lookups and erases (backward-shift deletion across the
