@@ -320,11 +320,15 @@ def rawalign_dtw_submit_chunks(h, chunks, events, cands):
     return tickets, status
 
 
-def rawalign_dtw_poll_chunks(h, tickets, cap: int, timeout_us: int = -1):
+def rawalign_dtw_poll_chunks(h, tickets, cap: int, timeout_us: int = -1, out=None):
     """Results of every ticket, back to back, and the count per ticket; None
-    while RA_ENOTREADY."""
+    while RA_ENOTREADY.  out: optional contiguous RESULT_DTYPE array of at
+    least cap records, reused across calls; the results are then a view of it."""
     t = np.ascontiguousarray(tickets, np.uint64)
-    out = np.zeros(max(int(cap), 1), RESULT_DTYPE)
+    if out is None:
+        out = np.zeros(max(int(cap), 1), RESULT_DTYPE)
+    elif out.dtype != RESULT_DTYPE or not out.flags.c_contiguous or len(out) < cap:
+        raise TypeError("out must be a contiguous RESULT_DTYPE array of at least cap records")
     counts = np.zeros(len(t), np.uint32)
     code = load().rawalign_dtw_poll_chunks(h, _ptr(t), len(t), _ptr(out), int(cap), _ptr(counts), int(timeout_us))
     if code == RA_ENOTREADY:

@@ -122,6 +122,7 @@ class ServingLoop:
         t0 = time.perf_counter()
         next_arrival = t0
         gen_cap = in_flight if realtime else max(1, -(-in_flight // max(1, generations)))
+        res_buf = np.zeros(0, B.RESULT_DTYPE)  # poll_chunks writes here (grown on demand, reused)
 
         while True:
             now = time.perf_counter()
@@ -193,8 +194,11 @@ class ServingLoop:
                 tk, qs, ts, ctk = gens[0]
                 must = (not realtime) and (len(gens) >= generations or not idle.any())
                 a = time.perf_counter()
-                got = B.rawalign_dtw_poll_chunks(h, np.concatenate([tk, ctk]) if len(ctk) else tk,
-                                                 int(self.n_cand[qs].sum()) + 1, timeout_us=-1 if must else 0)
+                cap = int(self.n_cand[qs].sum()) + 1
+                if len(res_buf) < cap:
+                    res_buf = np.zeros(2 * cap, B.RESULT_DTYPE)
+                got = B.rawalign_dtw_poll_chunks(h, np.concatenate([tk, ctk]) if len(ctk) else tk, cap,
+                                                 timeout_us=-1 if must else 0, out=res_buf)
                 t_poll += time.perf_counter() - a
                 if got is None:
                     break
@@ -207,9 +211,12 @@ class ServingLoop:
                 st.cells += int(res["cells"].sum())
                 # a chunk's results carry its read's decision (every candidate the same)
                 starts = np.cumsum(counts) - counts
-                dec = np.full(len(tk), B.RA_PENDING, np.int64)
                 has = counts > 0
-                dec[has] = res["decision"][starts[has]]
+                if has.all():
+                    dec = res["decision"][starts].astype(np.int64)
+                else:
+                    dec = np.full(len(tk), B.RA_PENDING, np.int64)
+                    dec[has] = res["decision"][starts[has]]
                 busy[qs] = False
                 ready_at[qs] = ts + chunk_s if realtime else tv
                 at_end = pos[qs] >= self.n_ev[qs]
