@@ -143,12 +143,17 @@ def test_missing_library_fails_loudly(tmp_path):
 
 
 def test_poll_rejects_an_unusable_output_buffer():
-    """rawalign_dtw_poll(out=...) writes into the caller's array only when it
-    can hold cap records of the result layout; anything else is refused
-    before the library is called."""
+    """rawalign_dtw_poll(out=...) and rawalign_dtw_poll_chunks(out=...) write
+    into the caller's array only when it can hold cap records of the result
+    layout; anything else is refused before the library is called."""
     with pytest.raises(TypeError):
         B.rawalign_dtw_poll(None, 1, 4, out=np.zeros(4, np.float64))
     with pytest.raises(TypeError):
         B.rawalign_dtw_poll(None, 1, 4, out=np.zeros(3, B.RESULT_DTYPE))
     with pytest.raises(TypeError):
         B.rawalign_dtw_poll(None, 1, 4, out=np.zeros(8, B.RESULT_DTYPE)[::2])
+    tickets = np.arange(1, 3, dtype=np.uint64)
+    with pytest.raises(TypeError):
+        B.rawalign_dtw_poll_chunks(None, tickets, 4, out=np.zeros(4, np.float64))
+    with pytest.raises(TypeError):
+        B.rawalign_dtw_poll_chunks(None, tickets, 4, out=np.zeros(3, B.RESULT_DTYPE))
